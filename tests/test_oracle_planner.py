@@ -1,0 +1,273 @@
+"""Pins for the oracle planner (CPU only).
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden), dense matrices (textbook Pauli and gate
+matrices), or invariants that any correct planner must satisfy.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import planner as P
+from workloads import (from_strings, heisenberg_lattice, pauli_to_masks, tfim_chain,
+                       random_klocal, jw_like, gradient_2local)
+from tests import dense as D
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read(name):
+    out = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            out.setdefault(key, []).append(vals)
+    return out
+
+
+def _parse_gate(tok):
+    for k in ("CNOT", "CZ", "H", "S"):
+        if tok.startswith(k):
+            rest = tok[len(k):]
+            if "," in rest:
+                a, b = rest.split(",")
+                return (k, int(a), int(b))
+            return (k, int(rest), -1)
+    raise ValueError(tok)
+
+
+# ---------------------------------------------------------------- gate rules
+
+def test_conjugation_tables_match_rules_and_dense():
+    lines = []
+    with open(os.path.join(GOLD, "conjugation_tables.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                lines.append(line.split())
+    assert len(lines) == 24
+    for gname, p, q in lines:
+        n = len(p)
+        gate = (gname, 0, -1) if n == 1 else (gname, 0, 1)
+        x, z = pauli_to_masks(p)
+        sign = 1 if q[0] == "-" else 0
+        qx, qz = pauli_to_masks(q[1:])
+        assert P.apply_gate_row(gate, x, z, 0) == (qx, qz, sign), (gname, p, q)
+        U = D.gate(n, gate)
+        lhs = U @ D.pauli(n, x, z) @ U.conj().T
+        rhs = (-1) ** sign * D.pauli(n, qx, qz)
+        assert np.allclose(lhs, rhs), (gname, p, q)
+
+
+def test_gate_rules_exhaustive_dense():
+    n = 3
+    gates = [("H", q, -1) for q in range(n)] + [("S", q, -1) for q in range(n)]
+    gates += [(k, a, b) for k in ("CNOT", "CZ") for a in range(n) for b in range(n) if a != b]
+    for g in gates:
+        U = D.gate(n, g)
+        for x in range(8):
+            for z in range(8):
+                for r in (0, 1):
+                    x2, z2, r2 = P.apply_gate_row(g, x, z, r)
+                    lhs = (-1) ** r * U @ D.pauli(n, x, z) @ U.conj().T
+                    assert np.allclose(lhs, (-1) ** r2 * D.pauli(n, x2, z2)), (g, x, z)
+                # vectorised form agrees with the row form
+                X, Z, R = P.apply_gates_rows([g], [x], [z], [0])
+                assert (int(X[0]), int(Z[0]), int(R[0])) == P.apply_gate_row(g, x, z, 0)
+
+
+def test_printed_cnot_z_rule_is_a_misprint():
+    """Table 3 prints z_t ^= z_c for CNOT; Table 2 (I1Z2 -> Z1Z2) and dense
+    matrices need z_c ^= z_t.  The printed rule fails the dense check."""
+    n = 2
+    U = D.cnot(n, 0, 1)
+    x, z = pauli_to_masks("IZ")
+    printed = (x, z ^ ((z & 1) << 1), 0)   # z_t ^= z_c leaves IZ unchanged
+    lhs = U @ D.pauli(n, x, z) @ U.conj().T
+    assert not np.allclose(lhs, D.pauli(n, printed[0], printed[1]))
+    assert P.apply_gate_row(("CNOT", 0, 1), x, z, 0) == pauli_to_masks("ZZ") + (0,)
+
+
+# ---------------------------------------------------------------- worked examples
+
+def test_worked_example_gate_list_and_diagonal():
+    g = _read("worked_example.txt")
+    terms = g["terms"][0]
+    gates_exp = [_parse_gate(t) for t in g["gates"][0]]
+    diag = g["diag"][0]
+    xs, zs = zip(*(pauli_to_masks(t) for t in terms))
+    gates, masks, signs = P.synthesize_group(4, xs, zs, skip_rule=P.SKIP_PAPER)
+    assert gates == gates_exp
+    for mk, sg, d in zip(masks, signs, diag):
+        assert sg == (1 if d[0] == "-" else 0)
+        assert pauli_to_masks(d[1:]) == (0, mk)
+    # the same result under every skip rule (no qubit of this group is skipped)
+    for rule in (P.SKIP_NONE, P.SKIP_Y):
+        assert P.synthesize_group(4, xs, zs, skip_rule=rule) == (gates, masks, signs)
+    # dense: C H C^dag is the printed diagonal operator
+    C = D.circuit(4, gates)
+    H = sum(D.pauli(4, a, b) for a, b in zip(xs, zs))
+    Hd = sum((-1 if d[0] == "-" else 1) * D.pauli(4, *pauli_to_masks(d[1:])) for d in diag)
+    assert np.allclose(C @ H @ C.conj().T, Hd)
+    assert np.allclose(Hd, np.diag(np.diag(Hd)))
+
+
+def test_appendix_independent_rows():
+    g = _read("appendix_independence.txt")
+    terms = g["terms"][0]
+    rows = [int(v) - 1 for v in g["rows"][0]]
+    n = 4
+    packed = [x | (z << n) for x, z in (pauli_to_masks(t) for t in terms)]
+    assert P.linearly_independent_terms(packed, 2 * n) == rows
+
+
+def test_independent_rows_span_the_group():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        n = int(rng.integers(2, 7))
+        k = int(rng.integers(1, 12))
+        rows = [int(v) for v in rng.integers(0, 1 << (2 * n), size=k)]
+        sel = P.linearly_independent_terms(rows, 2 * n)
+        assert P.gf2_rank([rows[i] for i in sel]) == len(sel) == P.gf2_rank(rows)
+
+
+# ---------------------------------------------------------------- random groups
+
+def _random_groups(rng, n, m, weights=(1, 2, 3)):
+    h = random_klocal(n, m, rng, weights=tuple(w for w in weights if w <= n))
+    return h, P.greedy_partition(h.x, h.z)
+
+
+@pytest.mark.parametrize("rule", [P.SKIP_NONE, P.SKIP_PAPER, P.SKIP_Y])
+def test_random_groups_diagonalised_dense(rule):
+    rng = np.random.default_rng(11 + rule)
+    count = 0
+    for _ in range(25):
+        n = int(rng.integers(2, 6))
+        h, groups = _random_groups(rng, n, int(rng.integers(3, 14)))
+        for g in groups:
+            xs = [int(h.x[j]) for j in g]
+            zs = [int(h.z[j]) for j in g]
+            gates, masks, signs = P.synthesize_group(n, xs, zs, skip_rule=rule)
+            C = D.circuit(n, gates)
+            for a, b, mk, sg in zip(xs, zs, masks, signs):
+                lhs = C @ D.pauli(n, a, b) @ C.conj().T
+                assert np.allclose(lhs, (-1) ** sg * D.pauli(n, 0, mk))
+            count += 1
+    assert count > 40
+
+
+def test_rank_deficient_groups_never_fail():
+    """Many small groups are rank deficient; with the completion reading the
+    synthesis never fails (zero padding as printed fails on about a third)."""
+    rng = np.random.default_rng(3)
+    deficient = 0
+    for _ in range(150):
+        n = int(rng.integers(3, 9))
+        h, groups = _random_groups(rng, n, int(rng.integers(4, 30)), weights=(2, 3, 4))
+        for g in groups:
+            xs = [int(h.x[j]) for j in g]
+            zs = [int(h.z[j]) for j in g]
+            rank = P.gf2_rank([a | (b << n) for a, b in zip(xs, zs)])
+            deficient += rank < n
+            for rule in (P.SKIP_NONE, P.SKIP_Y):
+                P.synthesize_group(n, xs, zs, skip_rule=rule)  # raises on failure
+    assert deficient > 100
+
+
+def test_large_groups_row_and_vector_rules_agree():
+    rng = np.random.default_rng(8)
+    h = random_klocal(32, 400, rng, weights=(2, 3, 4))
+    groups = P.greedy_partition(h.x, h.z)
+    for g in groups[:6]:
+        xs = [int(h.x[j]) for j in g]
+        zs = [int(h.z[j]) for j in g]
+        gates, masks, signs = P.synthesize_group(32, xs, zs)
+        for a, b, mk, sg in zip(xs, zs, masks, signs):
+            r = (a, b, 0)
+            for gt in gates:
+                r = P.apply_gate_row(gt, *r)
+            assert r == (0, mk, sg)
+
+
+# ---------------------------------------------------------------- partition
+
+def _check_partition(h, groups):
+    seen = sorted(j for g in groups for j in g)
+    assert seen == list(range(h.m))
+    for gi, g in enumerate(groups):
+        assert g == sorted(g)
+        for a in g:
+            for b in g:
+                assert P.commutes(int(h.x[a]), int(h.z[a]), int(h.x[b]), int(h.z[b]))
+        # first fit: every member conflicts with each earlier group at insertion time
+        for j in g:
+            for g2 in groups[:gi]:
+                assert any(not P.commutes(int(h.x[j]), int(h.z[j]), int(h.x[k]), int(h.z[k]))
+                           for k in g2 if k < j)
+
+
+def test_partition_first_fit_invariants():
+    rng = np.random.default_rng(21)
+    for _ in range(10):
+        h, groups = _random_groups(rng, int(rng.integers(3, 10)), int(rng.integers(5, 60)))
+        _check_partition(h, groups)
+
+
+def test_partition_of_model_hamiltonians():
+    t = tfim_chain(10)
+    g = P.greedy_partition(t.x, t.z)
+    assert [len(v) for v in g] == [9, 10]
+    h30 = heisenberg_lattice(5, 6)
+    assert h30.m == 147 and h30.n == 30
+    g = P.greedy_partition(h30.x, h30.z)
+    assert [len(v) for v in g] == [49, 49, 49]
+    h32 = heisenberg_lattice(6, 6, drop_corners=True)
+    assert h32.n == 32 and h32.m == 156
+    assert len(P.greedy_partition(h32.x, h32.z)) == 3
+    _check_partition(t, P.greedy_partition(t.x, t.z))
+
+
+def test_skip_rule_on_heisenberg_groups():
+    h = heisenberg_lattice(2, 3)
+    pl = P.plan(h.n, h.x, h.z, skip_rule=P.SKIP_Y)
+    assert pl.gates[0] == [("H", q, -1) for q in range(h.n)]
+    assert pl.gates[1] == [g for q in range(h.n) for g in (("S", q, -1), ("H", q, -1))]
+    assert pl.gates[2] == []
+    # XX -> ZZ (+), YY -> -Z -Z = +ZZ, ZZ unchanged
+    for gi in range(3):
+        assert all(s == 0 for s in pl.signs[gi])
+    pl0 = P.plan(h.n, h.x, h.z, skip_rule=P.SKIP_NONE)
+    assert any(k == "CNOT" for k, _, _ in pl0.gates[0])
+
+
+def test_workload_term_counts():
+    assert jw_like().m == 20000
+    assert gradient_2local().m == 200
+
+
+def test_cnot_layer_matrix_is_the_cnot_permutation():
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        n = 5
+        gates = []
+        for _ in range(8):
+            c, t = (int(v) for v in rng.choice(n, 2, replace=False))
+            gates.append(("CNOT", c, t))
+        A, Ainv = P.cnot_layer_matrix(gates, n)
+        U = D.circuit(n, gates)
+        for v in range(1 << n):
+            img = 0
+            for q in range(n):
+                if (v >> q) & 1:
+                    img ^= A[q]
+            assert U[img, v] == 1
+            back = 0
+            for q in range(n):
+                if (img >> q) & 1:
+                    back ^= Ainv[q]
+            assert back == v
