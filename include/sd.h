@@ -1,0 +1,188 @@
+/*
+ * sd.h -- C ABI of the simultaneous-diagonalisation Trotter simulator.
+ *
+ * The method (Kawase & Fujii, arXiv:2206.11664): the Hamiltonian
+ * H = sum_j c_j P_j (Sec. 2.2, real c_j, P_j in {I,X,Y,Z}^n) is split on the
+ * host into groups of mutually commuting terms (Sec. 2.3, greedy); each
+ * group g is mapped by a Clifford circuit C_g found with the binary tableau
+ * (Sec. 2.4 and 3.2, Algorithms 1-6) to diagonal Z-strings,
+ *     P_j = C_g^dag (-1)^{r_j} Z^{m_j} C_g            (Eq. hami_sim_diag),
+ * and one Trotter step applies, group after group, C_g, the diagonal phase
+ *     psi[x] *= exp(-i dt sum_j c_j (-1)^{r_j + |x & m_j|})   (Sec. 3.4 item 3)
+ * and C_g^dag (Eq. trotter_simul_diag).  All state-vector work runs in
+ * CUDA kernels for sm_103a; the host does planning and scheduling only.
+ *
+ * Conventions.
+ *   - Qubit q (the paper's qubit q+1) is bit q of every mask and of the
+ *     amplitude index (Sec. 2.1 numbers basis states with qubit 1 as the
+ *     least significant digit).
+ *   - A Pauli string is a pair of n-bit masks (x, z): I (0,0), X (1,0),
+ *     Z (0,1), Y (1,1).  Text strings: character q is qubit q.
+ *   - A state is 2^n contiguous amplitudes in device memory, interleaved
+ *     (re, im): float pairs for SD_C64, double pairs for SD_C128.
+ *
+ * Errors.  Every call returns an sd_status; on failure nothing the caller
+ * owns has been modified, except that a CUDA error (SD_ECUDA) or a timeout
+ * raised after kernels were launched may leave the state partly updated.
+ * sd_last_error() returns a message for the last failing call on a
+ * context.  A context is not thread safe.
+ *
+ * Ownership.  The library copies terms and coefficients, owns the plan and
+ * every device work buffer it allocates; the caller owns state buffers and
+ * host output arrays.  No call frees or reallocates caller memory.
+ *
+ * Ordering.  sd_evolve, sd_evolve_observe, sd_evolve_pauli and
+ * sd_evolve_batch are asynchronous on the given CUDA stream (NULL = legacy
+ * default stream); sd_expect and sd_grad synchronise the stream to return
+ * host values.
+ */
+#ifndef SD_H
+#define SD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sd_ctx sd_ctx;
+
+typedef enum {
+    SD_OK = 0,
+    SD_EINVAL = 1,     /* invalid argument; nothing modified */
+    SD_ENOMEM = 2,     /* host or device allocation failed */
+    SD_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    SD_ENOPLAN = 4,    /* sd_plan has not been called on this context */
+    SD_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    SD_EINTERNAL = 6   /* a planner invariant failed (e.g. a term not diagonal) */
+} sd_status;
+
+typedef enum { SD_C64 = 0, SD_C128 = 1 } sd_dtype;
+
+/* Gate kinds in plan views (application order). */
+enum { SD_GATE_H = 0, SD_GATE_S = 1, SD_GATE_CNOT = 2, SD_GATE_CZ = 3 };
+
+/* Planner options (sd_plan).  Zero-initialised = defaults. */
+typedef struct {
+    /* Skip rule of Sec. 3.2 (after Algorithm 5): 0 = none (every qubit goes
+     * through steps (i)-(iv)); 1 = the paper's rule (qubits carrying only
+     * I/Z are left alone, only I/X get H, both leave steps (i)-(iv));
+     * 2 = rule 1 plus qubits carrying only I/Y get S then H.  -1 = default (2). */
+    int skip_rule;
+    /* Tile size of the state-vector passes, log2 amplitudes per CTA tile:
+     * 0 = chosen by the autotuner, else 9..13. */
+    int tile_bits;
+    int reserved[6];
+} sd_plan_opts;
+
+/* Read-only view of a plan; pointers stay valid until the next sd_plan or
+ * sd_destroy on the context. */
+typedef struct {
+    int n;
+    int64_t m;
+    int64_t n_groups;
+    const int64_t *group_offsets;  /* n_groups + 1 offsets into group_terms   */
+    const int64_t *group_terms;    /* m term indices, grouped, input order    */
+    const uint64_t *masks;         /* m: Z mask m_j of C_g P_j C_g^dag         */
+    const uint8_t *signs;          /* m: sign bit r_j                          */
+    const int64_t *gate_offsets;   /* n_groups + 1 offsets (in gates)          */
+    const int32_t *gates;          /* 3 int32 per gate: kind, a, b (b=-1 for 1q) */
+    const uint64_t *cnot_cols;     /* n_groups * n: A_g e_q for the CNOT map x -> A_g x */
+    const uint64_t *cnot_inv_cols; /* n_groups * n: A_g^-1 e_q                 */
+} sd_plan_view;
+
+/* Schedule statistics for one Trotter step of the tile path. */
+typedef struct {
+    int tile_bits;            /* K: log2 amplitudes per tile                */
+    int64_t passes_per_step;  /* state passes (HBM read + write) per step  */
+    int64_t rounds_per_step;  /* register rounds over all passes           */
+    int64_t diag_passes;      /* passes that apply a group phase            */
+    int onchip;               /* 1 if the whole state stays on chip (small n) */
+} sd_schedule_stats;
+
+/* Create a context for H = sum_j coeffs[j] * P_(xmask[j], zmask[j]) on n
+ * qubits (Sec. 2.2).  1 <= n <= 40, m >= 1; a mask bit at or above n gives
+ * SD_EINVAL.  Identity terms are allowed (a global phase).  Inputs are
+ * copied. */
+sd_status sd_create(int n, int64_t m, const uint64_t *xmask, const uint64_t *zmask,
+                    const double *coeffs, sd_ctx **out);
+
+/* Same, from text strings of length n over {I,X,Y,Z} (character q = qubit q). */
+sd_status sd_create_str(int n, int64_t m, const char *const *paulis, const double *coeffs,
+                        sd_ctx **out);
+
+/* Replace the m coefficients (input term order) of a context.  The plan
+ * (groups, circuits, masks) depends only on the Pauli strings and is kept;
+ * device programs built for the old coefficients are dropped. */
+sd_status sd_set_coeffs(sd_ctx *ctx, const double *coeffs);
+
+/* Host planning: greedy first-fit partition into commuting groups (Sec. 2.3),
+ * independent generators (Appendix, Algorithm 6) completed to n commuting
+ * rows, synthesis steps (i)-(iv) (Algorithms 2-5), and masks/signs of every
+ * term by replaying the circuit on the full tableau (Eq. hami_sim_diag).
+ * opts may be NULL.  Host only: no device memory is touched here. */
+sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts);
+
+sd_status sd_get_plan(const sd_ctx *ctx, sd_plan_view *out);
+
+/* Statistics of the pass schedule that sd_evolve would run for this dtype
+ * and Trotter order (1 or 2).  Host only. */
+sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_stats *out);
+
+/* Trotter evolution in place (Eq. trotter_simul_diag): `steps` steps of
+ * size dt of order 1 (groups 1..G) or 2 (Strang: groups 1..G-1 at dt/2, G
+ * at dt, G-1..1 at dt/2; the half steps of group 1 that meet between
+ * consecutive steps of one call are merged).  d_state: 2^n amplitudes of
+ * `dtype` in device memory, owned by the caller.  Phases are formed from
+ * angles dt*c_j/(2 pi) reduced mod 1 in FP64 and summed exactly in Q0.64
+ * fixed point. */
+sd_status sd_evolve(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt, int64_t steps,
+                    int order, void *cuda_stream);
+
+/* As sd_evolve, and after every step writes <psi|O|psi> for the Pauli-sum
+ * observable O = sum_k oc[k] P_(ox[k], oz[k]) into d_trace[step] (device
+ * memory, `steps` doubles, caller-owned). */
+sd_status sd_evolve_observe(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt,
+                            int64_t steps, int order, int64_t mo, const uint64_t *ox,
+                            const uint64_t *oz, const double *oc, double *d_trace,
+                            void *cuda_stream);
+
+/* Baseline path (Eq. trotter_decomp without grouping, Sec. 4): one state pass
+ * per term, psi <- (cos a - i sin a P_j) psi with a = c_j dt, terms in
+ * group order (so the product equals sd_evolve's up to rounding). */
+sd_status sd_evolve_pauli(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt,
+                          int64_t steps, int order, void *cuda_stream);
+
+/* <psi|O|psi> for O = sum_k oc[k] P_(ox[k], oz[k]) (host arrays, mo terms),
+ * reduced in FP64, written to *out_host.  Synchronises the stream. */
+sd_status sd_expect(sd_ctx *ctx, const void *d_state, sd_dtype dtype, int64_t mo,
+                    const uint64_t *ox, const uint64_t *oz, const double *oc,
+                    double *out_host, void *cuda_stream);
+
+/* Value f = <psi_T|O|psi_T> and gradient df/dc_j (m doubles, input term
+ * order) of the evolution sd_evolve(d_state0, dt, steps, order) by an
+ * adjoint sweep that undoes each group exponential (no checkpoints).
+ * d_state0 is not modified; two device work vectors of the state's size are
+ * allocated by the library and kept for later calls. */
+sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt,
+                  int64_t steps, int order, int64_t mo, const uint64_t *ox,
+                  const uint64_t *oz, const double *oc, double *value_out,
+                  double *grad_out, void *cuda_stream);
+
+/* Evolve `count` independent problems (each its own planned context and
+ * device state, qubit counts may differ) with the same dt/steps/order,
+ * as one CUDA graph launch per call. */
+sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t count,
+                          sd_dtype dtype, double dt, int64_t steps, int order,
+                          void *cuda_stream);
+
+/* Message for the last failing call on ctx (ctx may be NULL: last global error). */
+const char *sd_last_error(const sd_ctx *ctx);
+
+void sd_destroy(sd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SD_H */

@@ -1,0 +1,801 @@
+// C ABI (include/sd.h): contexts, planning, device programs and the drivers
+// of evolution, expectation and gradient.  All state-vector work is done by
+// the kernels in kernels.cu; this file only plans, schedules, uploads and
+// launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sd.h"
+#include "kernels.cuh"
+#include "sd_internal.h"
+
+using namespace sd;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Device program of one circuit: either a pass schedule (tile path) or a
+// flat op list (on-chip path).
+struct Program {
+    bool onchip = false;
+    DevSchedule sched;
+    DevCircuit circ;
+    std::vector<void *> allocs;
+    int64_t passes = 0, rounds = 0, diag_passes = 0;
+};
+
+struct GradGroup {   // per (group, fraction): class-sorted terms for the adjoint kernel
+    DevGrad g{};
+    uint64_t *masks_f = nullptr;
+    int64_t *qinv = nullptr;
+    int32_t *term_id = nullptr;
+    double *factor = nullptr;
+};
+
+void free_program(Program &p) {
+    for (void *a : p.allocs) cudaFree(a);
+    p.allocs.clear();
+}
+
+}  // namespace
+
+struct sd_ctx {
+    int n = 0;
+    int64_t m = 0;
+    std::vector<uint64_t> x, z;
+    std::vector<double> c;
+    bool planned = false;
+    Plan plan;
+    int tile_bits_opt = 0;
+    // plan view storage
+    std::vector<int64_t> v_goff, v_gterms, v_gateoff;
+    std::vector<uint64_t> v_masks, v_cols, v_icols;
+    std::vector<uint8_t> v_signs;
+    std::vector<int32_t> v_gates;
+    std::string err;
+    // device side
+    int num_sms = 0;
+    std::map<std::tuple<int, int, int, double>, std::unique_ptr<Program>> programs;
+    std::map<std::tuple<int, int, int>, std::unique_ptr<Program>> cliff_programs;   // (dtype, group, fwd)
+    std::map<std::pair<int, double>, GradGroup> grad_groups;
+    std::vector<void *> grad_allocs;
+    double *d_partial = nullptr;
+    size_t partial_cap = 0;
+    double *d_scalar = nullptr;
+    uint64_t *d_obs = nullptr;   // ox | oz | oc staging
+    size_t obs_cap = 0;
+    void *d_work[2] = {nullptr, nullptr};
+    size_t work_bytes = 0;
+    double *d_gacc = nullptr;
+    double grad_dt = 0.0;
+
+    ~sd_ctx() {
+        for (auto &kv : programs) free_program(*kv.second);
+        for (auto &kv : cliff_programs) free_program(*kv.second);
+        for (void *a : grad_allocs) cudaFree(a);
+        cudaFree(d_partial);
+        cudaFree(d_scalar);
+        cudaFree(d_obs);
+        cudaFree(d_work[0]);
+        cudaFree(d_work[1]);
+        cudaFree(d_gacc);
+    }
+};
+
+namespace {
+
+sd_status fail(sd_ctx *ctx, sd_status s, const std::string &msg) {
+    g_last_error = msg;
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, SD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t upload(std::vector<void *> &allocs, T *&dst, const std::vector<T> &src) {
+    size_t bytes = sizeof(T) * std::max<size_t>(src.size(), 1);
+    cudaError_t e = cudaMalloc((void **)&dst, bytes);
+    if (e != cudaSuccess) return e;
+    allocs.push_back(dst);
+    if (!src.empty()) e = cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+sd_status ensure_device(sd_ctx *ctx) {
+    if (ctx->num_sms) return SD_OK;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    return SD_OK;
+}
+
+int default_tile_bits(const sd_ctx *ctx, bool dbl) {
+    int K = ctx->tile_bits_opt > 0 ? ctx->tile_bits_opt : (dbl ? 12 : 13);
+    return std::min(K, ctx->n);
+}
+
+bool use_onchip(const sd_ctx *ctx, bool dbl) { return ctx->n <= onchip_max_qubits(dbl); }
+
+// Build and upload a program for a circuit.
+sd_status build_program(sd_ctx *ctx, const Circuit &circ, bool dbl, Program &P) {
+    P.onchip = use_onchip(ctx, dbl);
+    const int n = ctx->n;
+    if (P.onchip) {
+        std::vector<DevFlatOp> ops;
+        for (auto &o : circ.ops) ops.push_back(DevFlatOp{o.kind, o.q, o.q2, o.idx});
+        std::vector<DevDiagFlat> dg;
+        std::vector<uint64_t> dm;
+        std::vector<int64_t> dq;
+        for (auto &d : circ.diags) {
+            dg.push_back(DevDiagFlat{(int64_t)dm.size(), (int64_t)d.masks.size()});
+            dm.insert(dm.end(), d.masks.begin(), d.masks.end());
+            dq.insert(dq.end(), d.q.begin(), d.q.end());
+        }
+        std::vector<uint64_t> sp, smk, up;
+        for (auto &L : circ.phases) {
+            sp.push_back(L.sp);
+            smk.push_back(L.sm);
+            up.insert(up.end(), L.up.begin(), L.up.end());
+        }
+        DevCircuit &C = P.circ;
+        C.n_ops = (int64_t)ops.size();
+        CK(upload(P.allocs, C.ops, ops));
+        CK(upload(P.allocs, C.diags, dg));
+        CK(upload(P.allocs, C.dmasks, dm));
+        CK(upload(P.allocs, C.dq, dq));
+        CK(upload(P.allocs, C.phase_sp, sp));
+        CK(upload(P.allocs, C.phase_sm, smk));
+        CK(upload(P.allocs, C.phase_up, up));
+        P.passes = 0;
+        return SD_OK;
+    }
+    Schedule S;
+    int K = default_tile_bits(ctx, dbl);
+    int c = dbl ? 3 : 4;
+    std::string e = schedule_circuit(circ, n, K, c, S);
+    if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
+    DevSchedule &D = P.sched;
+    D.K = S.K;
+    D.c = S.c;
+    D.n_passes = (int64_t)S.passes.size();
+    D.host_passes = S.passes;
+    CK(upload(P.allocs, D.passes, S.passes));
+    CK(upload(P.allocs, D.rounds, S.rounds));
+    CK(upload(P.allocs, D.ops, S.ops));
+    CK(upload(P.allocs, D.perms, S.perms));
+    CK(upload(P.allocs, D.diags, S.diags));
+    CK(upload(P.allocs, D.phases, S.phases));
+    CK(upload(P.allocs, D.term_masks, S.term_masks));
+    CK(upload(P.allocs, D.term_q, S.term_q));
+    CK(upload(P.allocs, D.mask_pool, S.mask_pool));
+    P.passes = (int64_t)S.passes.size();
+    P.rounds = (int64_t)S.rounds.size();
+    P.diag_passes = S.diag_passes;
+    return SD_OK;
+}
+
+// Group order and fractions of one Trotter step.
+std::vector<std::pair<int, double>> step_sequence(int G, int order) {
+    std::vector<std::pair<int, double>> s;
+    if (order == 1 || G == 1) {
+        for (int g = 0; g < G; g++) s.push_back({g, 1.0});
+        return s;
+    }
+    for (int g = 0; g < G - 1; g++) s.push_back({g, 0.5});
+    s.push_back({G - 1, 1.0});
+    for (int g = G - 2; g >= 0; g--) s.push_back({g, 0.5});
+    return s;
+}
+
+// Segments of an evolution: kind 0 = one unmerged step, 1 = head, 2 = core, 3 = tail
+// (second order with half steps of group 0 merged across steps).
+Circuit segment_circuit(const sd_ctx *ctx, int order, int kind, double dt) {
+    Circuit c;
+    const int G = (int)ctx->plan.groups.size();
+    auto add = [&](int g, double f) { append_group_step(ctx->plan, g, f, dt, ctx->c, c); };
+    if (kind == 0 || order == 1 || G == 1) {
+        for (auto &p : step_sequence(G, order)) add(p.first, p.second);
+        return c;
+    }
+    if (kind == 1) {
+        add(0, 0.5);
+        return c;
+    }
+    for (int g = 1; g < G - 1; g++) add(g, 0.5);
+    add(G - 1, 1.0);
+    for (int g = G - 2; g >= 1; g--) add(g, 0.5);
+    add(0, kind == 2 ? 1.0 : 0.5);
+    return c;
+}
+
+sd_status get_program(sd_ctx *ctx, bool dbl, int order, int kind, double dt, Program *&out) {
+    auto key = std::make_tuple((int)dbl, order, kind, dt);
+    auto it = ctx->programs.find(key);
+    if (it != ctx->programs.end()) {
+        out = it->second.get();
+        return SD_OK;
+    }
+    // keep the cache small: programs for other dt values are dropped
+    for (auto i = ctx->programs.begin(); i != ctx->programs.end();) {
+        if (std::get<3>(i->first) != dt) {
+            free_program(*i->second);
+            i = ctx->programs.erase(i);
+        } else {
+            ++i;
+        }
+    }
+    auto P = std::make_unique<Program>();
+    Circuit c = segment_circuit(ctx, order, kind, dt);
+    sd_status s = build_program(ctx, c, dbl, *P);
+    if (s != SD_OK) {
+        free_program(*P);
+        return s;
+    }
+    out = P.get();
+    ctx->programs[key] = std::move(P);
+    return SD_OK;
+}
+
+sd_status run_program(sd_ctx *ctx, bool dbl, Program &P, void *psi, int64_t reps, cudaStream_t st,
+                      const uint64_t *d_oz = nullptr, const double *d_oc = nullptr, int nobs = 0,
+                      double *d_trace = nullptr) {
+    if (reps <= 0) return SD_OK;
+    if (P.onchip) {
+        if (P.circ.n_ops == 0 && nobs == 0) return SD_OK;
+        CK(launch_onchip(dbl, psi, ctx->n, P.circ, reps, d_oz, d_oc, nobs, d_trace, st));
+        return SD_OK;
+    }
+    for (int64_t r = 0; r < reps; r++)
+        for (int64_t p = 0; p < P.sched.n_passes; p++)
+            CK(launch_tile_pass(dbl, psi, ctx->n, P.sched, (int)p, ctx->num_sms, st));
+    return SD_OK;
+}
+
+sd_status check_state_args(sd_ctx *ctx, const void *state, sd_dtype dtype, int order) {
+    if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
+    if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");
+    if (!state) return fail(ctx, SD_EINVAL, "null state pointer");
+    if (dtype != SD_C64 && dtype != SD_C128) return fail(ctx, SD_EINVAL, "dtype must be SD_C64 or SD_C128");
+    if (order != 1 && order != 2) return fail(ctx, SD_EINVAL, "order must be 1 or 2");
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, state) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(ctx, SD_EINVAL, "state must be a device pointer");
+    }
+    return ensure_device(ctx);
+}
+
+sd_status evolve_impl(sd_ctx *ctx, void *psi, bool dbl, double dt, int64_t steps, int order,
+                      cudaStream_t st) {
+    const int G = (int)ctx->plan.groups.size();
+    Program *P = nullptr;
+    sd_status s;
+    if (order == 1 || G == 1 || steps == 1) {
+        if ((s = get_program(ctx, dbl, order, 0, dt, P)) != SD_OK) return s;
+        return run_program(ctx, dbl, *P, psi, steps, st);
+    }
+    Program *H = nullptr, *C = nullptr, *T = nullptr;
+    if ((s = get_program(ctx, dbl, order, 1, dt, H)) != SD_OK) return s;
+    if ((s = get_program(ctx, dbl, order, 2, dt, C)) != SD_OK) return s;
+    if ((s = get_program(ctx, dbl, order, 3, dt, T)) != SD_OK) return s;
+    if ((s = run_program(ctx, dbl, *H, psi, 1, st)) != SD_OK) return s;
+    if ((s = run_program(ctx, dbl, *C, psi, steps - 1, st)) != SD_OK) return s;
+    return run_program(ctx, dbl, *T, psi, 1, st);
+}
+
+sd_status ensure_partial(sd_ctx *ctx, size_t count) {
+    if (count <= ctx->partial_cap) return SD_OK;
+    cudaFree(ctx->d_partial);
+    ctx->d_partial = nullptr;
+    ctx->partial_cap = 0;
+    CK(cudaMalloc((void **)&ctx->d_partial, sizeof(double) * count));
+    ctx->partial_cap = count;
+    if (!ctx->d_scalar) CK(cudaMalloc((void **)&ctx->d_scalar, sizeof(double) * 4));
+    return SD_OK;
+}
+
+int expect_blocks(const sd_ctx *ctx) {
+    int64_t N = (int64_t)1 << ctx->n;
+    int64_t b = (N + 255) / 256;
+    int64_t cap = (int64_t)ctx->num_sms * 4;
+    return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// Observable staged on the device: diagonal terms (x = 0) packed for one
+// fused pass, the others kept on the host for one pass each.
+struct StagedObs {
+    int nd = 0;
+    const uint64_t *dz = nullptr;
+    const double *dc = nullptr;
+    std::vector<uint64_t> ox, oz;
+    std::vector<double> oc;
+};
+
+sd_status stage_obs(sd_ctx *ctx, int64_t mo, const uint64_t *ox, const uint64_t *oz, const double *oc,
+                    StagedObs &so) {
+    std::vector<uint64_t> dz;
+    std::vector<double> dcv;
+    so = StagedObs{};
+    for (int64_t k = 0; k < mo; k++) {
+        if (ox[k] == 0) {
+            dz.push_back(oz[k]);
+            dcv.push_back(oc[k]);
+        } else {
+            so.ox.push_back(ox[k]);
+            so.oz.push_back(oz[k]);
+            so.oc.push_back(oc[k]);
+        }
+    }
+    // full arrays too (for sd_grad's lambda = O phi): layout [dz | dc | ax | az | ac]
+    size_t need = dz.size() * 2 + (size_t)mo * 3 + 2;
+    if (need > ctx->obs_cap) {
+        cudaFree(ctx->d_obs);
+        ctx->d_obs = nullptr;
+        ctx->obs_cap = 0;
+        CK(cudaMalloc((void **)&ctx->d_obs, sizeof(uint64_t) * need));
+        ctx->obs_cap = need;
+    }
+    uint64_t *p = ctx->d_obs;
+    so.nd = (int)dz.size();
+    so.dz = p;
+    so.dc = reinterpret_cast<const double *>(p + dz.size());
+    if (!dz.empty()) {
+        CK(cudaMemcpy(p, dz.data(), sizeof(uint64_t) * dz.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p + dz.size(), dcv.data(), sizeof(double) * dcv.size(), cudaMemcpyHostToDevice));
+    }
+    uint64_t *q = p + 2 * dz.size();
+    CK(cudaMemcpy(q, ox, sizeof(uint64_t) * mo, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(q + mo, oz, sizeof(uint64_t) * mo, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(q + 2 * mo, oc, sizeof(double) * mo, cudaMemcpyHostToDevice));
+    return SD_OK;
+}
+
+const uint64_t *staged_all_x(sd_ctx *ctx, const StagedObs &so) { return ctx->d_obs + 2 * so.nd; }
+
+// <psi|O|psi> into d_out (device), asynchronously.
+sd_status expect_async(sd_ctx *ctx, const void *psi, bool dbl, const StagedObs &so, double *d_out,
+                       cudaStream_t st) {
+    const int blocks = expect_blocks(ctx);
+    size_t slots = (size_t)blocks * ((so.nd ? 1 : 0) + so.ox.size());
+    sd_status s = ensure_partial(ctx, std::max<size_t>(slots, 1));
+    if (s != SD_OK) return s;
+    int64_t off = 0;
+    if (so.nd) {
+        CK(launch_expect_diag(dbl, psi, ctx->n, so.dz, so.dc, so.nd, ctx->d_partial, blocks, st));
+        off += blocks;
+    }
+    for (size_t k = 0; k < so.ox.size(); k++) {
+        CK(launch_expect_pauli(dbl, psi, ctx->n, so.ox[k], so.oz[k], so.oc[k], ctx->d_partial + off,
+                               blocks, st));
+        off += blocks;
+    }
+    if (off == 0) {
+        CK(cudaMemsetAsync(d_out, 0, sizeof(double), st));
+        return SD_OK;
+    }
+    CK(launch_reduce(ctx->d_partial, off, d_out, 0, st));
+    return SD_OK;
+}
+
+sd_status check_obs(sd_ctx *ctx, int64_t mo, const uint64_t *ox, const uint64_t *oz, const double *oc) {
+    if (mo < 0 || (mo > 0 && (!ox || !oz || !oc))) return fail(ctx, SD_EINVAL, "invalid observable arrays");
+    const uint64_t lim = (uint64_t(1) << ctx->n) - 1;
+    for (int64_t k = 0; k < mo; k++)
+        if ((ox[k] & ~lim) || (oz[k] & ~lim) || !std::isfinite(oc[k]))
+            return fail(ctx, SD_EINVAL, "observable term " + std::to_string(k) + " is invalid");
+    return SD_OK;
+}
+
+sd_status get_cliff(sd_ctx *ctx, bool dbl, int g, bool fwd, Program *&out) {
+    auto key = std::make_tuple((int)dbl, g, (int)fwd);
+    auto it = ctx->cliff_programs.find(key);
+    if (it != ctx->cliff_programs.end()) {
+        out = it->second.get();
+        return SD_OK;
+    }
+    Circuit c;
+    append_clifford(ctx->plan, g, fwd, c);
+    auto P = std::make_unique<Program>();
+    if (c.ops.empty()) {
+        P->onchip = false;   // empty: nothing to run
+    } else {
+        sd_status s = build_program(ctx, c, dbl, *P);
+        if (s != SD_OK) {
+            free_program(*P);
+            return s;
+        }
+    }
+    out = P.get();
+    ctx->cliff_programs[key] = std::move(P);
+    return SD_OK;
+}
+
+bool program_empty(const Program &P) {
+    return P.onchip ? P.circ.n_ops == 0 : P.sched.n_passes == 0;
+}
+
+sd_status get_grad_group(sd_ctx *ctx, int g, double f, double dt, GradGroup *&out) {
+    auto key = std::make_pair(g, f);
+    auto it = ctx->grad_groups.find(key);
+    if (it != ctx->grad_groups.end()) {
+        out = &it->second;
+        return SD_OK;
+    }
+    const GroupPlan &gp = ctx->plan.groups[g];
+    std::vector<std::vector<size_t>> cls(16);
+    for (size_t k = 0; k < gp.terms.size(); k++) cls[gp.masks[k] & 15u].push_back(k);
+    std::vector<uint64_t> mf;
+    std::vector<int64_t> qi;
+    std::vector<int32_t> tid;
+    std::vector<double> fac;
+    GradGroup gg;
+    int off = 0;
+    const double inv2pi = 1.0 / (2.0 * M_PI);
+    for (int s = 0; s < 16; s++) {
+        gg.g.off[s] = off;
+        for (size_t k : cls[s]) {
+            double a = f * dt * ctx->c[gp.terms[k]];
+            double sg = gp.signs[k] ? -1.0 : 1.0;
+            mf.push_back(gp.masks[k] & ~uint64_t(15));
+            qi.push_back((int64_t)(0 - (uint64_t)turns_q64(sg * a * inv2pi)));
+            tid.push_back((int32_t)gp.terms[k]);
+            fac.push_back(2.0 * f * dt * sg);
+            off++;
+        }
+    }
+    gg.g.off[16] = off;
+    gg.g.m = off;
+    gg.g.base = 0;
+    CK(upload(ctx->grad_allocs, gg.masks_f, mf));
+    CK(upload(ctx->grad_allocs, gg.qinv, qi));
+    CK(upload(ctx->grad_allocs, gg.term_id, tid));
+    CK(upload(ctx->grad_allocs, gg.factor, fac));
+    ctx->grad_groups[key] = gg;
+    out = &ctx->grad_groups[key];
+    return SD_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+sd_status sd_create(int n, int64_t m, const uint64_t *xmask, const uint64_t *zmask,
+                    const double *coeffs, sd_ctx **out) {
+    if (!out) return fail(nullptr, SD_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (n < 1 || n > 40) return fail(nullptr, SD_EINVAL, "n must be in [1, 40]");
+    if (m < 1) return fail(nullptr, SD_EINVAL, "m must be >= 1");
+    if (!xmask || !zmask || !coeffs) return fail(nullptr, SD_EINVAL, "null term array");
+    const uint64_t lim = (n >= 64) ? ~uint64_t(0) : ((uint64_t(1) << n) - 1);
+    for (int64_t j = 0; j < m; j++) {
+        if ((xmask[j] & ~lim) || (zmask[j] & ~lim))
+            return fail(nullptr, SD_EINVAL, "term " + std::to_string(j) + " has a mask bit >= n");
+        if (!std::isfinite(coeffs[j]))
+            return fail(nullptr, SD_EINVAL, "term " + std::to_string(j) + " has a non-finite coefficient");
+    }
+    sd_ctx *ctx = new (std::nothrow) sd_ctx;
+    if (!ctx) return fail(nullptr, SD_ENOMEM, "out of host memory");
+    ctx->n = n;
+    ctx->m = m;
+    ctx->x.assign(xmask, xmask + m);
+    ctx->z.assign(zmask, zmask + m);
+    ctx->c.assign(coeffs, coeffs + m);
+    *out = ctx;
+    return SD_OK;
+}
+
+sd_status sd_create_str(int n, int64_t m, const char *const *paulis, const double *coeffs,
+                        sd_ctx **out) {
+    if (!out) return fail(nullptr, SD_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (!paulis || m < 1 || n < 1 || n > 40) return fail(nullptr, SD_EINVAL, "invalid arguments");
+    std::vector<uint64_t> x(m, 0), z(m, 0);
+    for (int64_t j = 0; j < m; j++) {
+        const char *s = paulis[j];
+        if (!s || (int)strlen(s) != n)
+            return fail(nullptr, SD_EINVAL, "string " + std::to_string(j) + " does not have length n");
+        for (int q = 0; q < n; q++) {
+            char ch = s[q];
+            if (ch >= 'a' && ch <= 'z') ch = char(ch - 'a' + 'A');
+            uint64_t b = uint64_t(1) << q;
+            if (ch == 'X') x[j] |= b;
+            else if (ch == 'Z') z[j] |= b;
+            else if (ch == 'Y') { x[j] |= b; z[j] |= b; }
+            else if (ch != 'I')
+                return fail(nullptr, SD_EINVAL, "string " + std::to_string(j) + " has a character outside IXYZ");
+        }
+    }
+    return sd_create(n, m, x.data(), z.data(), coeffs, out);
+}
+
+sd_status sd_set_coeffs(sd_ctx *ctx, const double *coeffs) {
+    if (!ctx || !coeffs) return fail(ctx, SD_EINVAL, "null argument");
+    for (int64_t j = 0; j < ctx->m; j++)
+        if (!std::isfinite(coeffs[j]))
+            return fail(ctx, SD_EINVAL, "term " + std::to_string(j) + " has a non-finite coefficient");
+    ctx->c.assign(coeffs, coeffs + ctx->m);
+    for (auto &kv : ctx->programs) free_program(*kv.second);
+    ctx->programs.clear();
+    for (void *p : ctx->grad_allocs) cudaFree(p);
+    ctx->grad_allocs.clear();
+    ctx->grad_groups.clear();
+    return SD_OK;
+}
+
+sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
+    if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
+    int rule = 2, tb = 0;
+    if (opts) {
+        rule = opts->skip_rule < 0 ? 2 : opts->skip_rule;
+        tb = opts->tile_bits;
+        if (rule > 2) return fail(ctx, SD_EINVAL, "skip_rule must be -1, 0, 1 or 2");
+        if (tb != 0 && (tb < 9 || tb > 13)) return fail(ctx, SD_EINVAL, "tile_bits must be 0 or 9..13");
+    }
+    Plan p;
+    std::string e = make_plan(ctx->n, ctx->m, ctx->x.data(), ctx->z.data(), rule, p);
+    if (!e.empty()) return fail(ctx, SD_EINTERNAL, "planner: " + e);
+    for (auto &kv : ctx->programs) free_program(*kv.second);
+    ctx->programs.clear();
+    for (auto &kv : ctx->cliff_programs) free_program(*kv.second);
+    ctx->cliff_programs.clear();
+    for (void *a : ctx->grad_allocs) cudaFree(a);
+    ctx->grad_allocs.clear();
+    ctx->grad_groups.clear();
+    ctx->plan = std::move(p);
+    ctx->tile_bits_opt = tb;
+    ctx->planned = true;
+    // plan view
+    const int n = ctx->n;
+    ctx->v_goff.assign(1, 0);
+    ctx->v_gterms.clear();
+    ctx->v_masks.clear();
+    ctx->v_signs.clear();
+    ctx->v_gateoff.assign(1, 0);
+    ctx->v_gates.clear();
+    ctx->v_cols.clear();
+    ctx->v_icols.clear();
+    for (auto &g : ctx->plan.groups) {
+        for (size_t k = 0; k < g.terms.size(); k++) {
+            ctx->v_gterms.push_back(g.terms[k]);
+            ctx->v_masks.push_back(g.masks[k]);
+            ctx->v_signs.push_back(g.signs[k]);
+        }
+        ctx->v_goff.push_back((int64_t)ctx->v_gterms.size());
+        for (auto &gt : g.gates) {
+            ctx->v_gates.push_back(gt.kind);
+            ctx->v_gates.push_back(gt.a);
+            ctx->v_gates.push_back(gt.b);
+        }
+        ctx->v_gateoff.push_back((int64_t)ctx->v_gates.size() / 3);
+        ctx->v_cols.insert(ctx->v_cols.end(), g.cnot_cols.begin(), g.cnot_cols.end());
+        ctx->v_icols.insert(ctx->v_icols.end(), g.cnot_inv_cols.begin(), g.cnot_inv_cols.end());
+    }
+    (void)n;
+    return SD_OK;
+}
+
+sd_status sd_get_plan(const sd_ctx *ctx, sd_plan_view *out) {
+    if (!ctx || !out) return fail(nullptr, SD_EINVAL, "null argument");
+    if (!ctx->planned) return fail(const_cast<sd_ctx *>(ctx), SD_ENOPLAN, "sd_plan has not been called");
+    out->n = ctx->n;
+    out->m = ctx->m;
+    out->n_groups = (int64_t)ctx->plan.groups.size();
+    out->group_offsets = ctx->v_goff.data();
+    out->group_terms = ctx->v_gterms.data();
+    out->masks = ctx->v_masks.data();
+    out->signs = ctx->v_signs.data();
+    out->gate_offsets = ctx->v_gateoff.data();
+    out->gates = ctx->v_gates.data();
+    out->cnot_cols = ctx->v_cols.data();
+    out->cnot_inv_cols = ctx->v_icols.data();
+    return SD_OK;
+}
+
+sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_stats *out) {
+    if (!ctx || !out) return fail(nullptr, SD_EINVAL, "null argument");
+    if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");
+    if (order != 1 && order != 2) return fail(ctx, SD_EINVAL, "order must be 1 or 2");
+    const bool dbl = dtype == SD_C128;
+    memset(out, 0, sizeof(*out));
+    out->onchip = use_onchip(ctx, dbl) ? 1 : 0;
+    if (out->onchip) return SD_OK;
+    const int G = (int)ctx->plan.groups.size();
+    Circuit c = segment_circuit(ctx, order, (order == 2 && G > 1) ? 2 : 0, 0.01);
+    Schedule S;
+    int K = default_tile_bits(ctx, dbl);
+    std::string e = schedule_circuit(c, ctx->n, K, dbl ? 3 : 4, S);
+    if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
+    out->tile_bits = K;
+    out->passes_per_step = (int64_t)S.passes.size();
+    out->rounds_per_step = (int64_t)S.rounds.size();
+    out->diag_passes = S.diag_passes;
+    return SD_OK;
+}
+
+sd_status sd_evolve(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt, int64_t steps, int order,
+                    void *cuda_stream) {
+    sd_status s = check_state_args(ctx, d_state, dtype, order);
+    if (s != SD_OK) return s;
+    if (steps < 0) return fail(ctx, SD_EINVAL, "steps must be >= 0");
+    if (!std::isfinite(dt)) return fail(ctx, SD_EINVAL, "dt must be finite");
+    if (steps == 0) return SD_OK;
+    return evolve_impl(ctx, d_state, dtype == SD_C128, dt, steps, order, (cudaStream_t)cuda_stream);
+}
+
+
+sd_status sd_evolve_observe(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt, int64_t steps,
+                            int order, int64_t mo, const uint64_t *ox, const uint64_t *oz,
+                            const double *oc, double *d_trace, void *cuda_stream) {
+    sd_status s = check_state_args(ctx, d_state, dtype, order);
+    if (s != SD_OK) return s;
+    if (steps < 0 || !std::isfinite(dt)) return fail(ctx, SD_EINVAL, "invalid steps or dt");
+    if ((s = check_obs(ctx, mo, ox, oz, oc)) != SD_OK) return s;
+    if (steps > 0 && !d_trace) return fail(ctx, SD_EINVAL, "null trace pointer");
+    if (steps == 0) return SD_OK;
+    const bool dbl = dtype == SD_C128;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    StagedObs so;
+    if ((s = stage_obs(ctx, mo, ox, oz, oc, so)) != SD_OK) return s;
+    Program *P = nullptr;
+    if ((s = get_program(ctx, dbl, order, 0, dt, P)) != SD_OK) return s;
+    if (P->onchip && so.ox.empty())
+        return run_program(ctx, dbl, *P, d_state, steps, st, so.dz, so.dc, so.nd, d_trace);
+    for (int64_t k = 0; k < steps; k++) {
+        if ((s = run_program(ctx, dbl, *P, d_state, 1, st)) != SD_OK) return s;
+        if ((s = expect_async(ctx, d_state, dbl, so, d_trace + k, st)) != SD_OK) return s;
+    }
+    return SD_OK;
+}
+
+sd_status sd_evolve_pauli(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt, int64_t steps,
+                          int order, void *cuda_stream) {
+    sd_status s = check_state_args(ctx, d_state, dtype, order);
+    if (s != SD_OK) return s;
+    if (steps < 0 || !std::isfinite(dt)) return fail(ctx, SD_EINVAL, "invalid steps or dt");
+    const bool dbl = dtype == SD_C128;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int G = (int)ctx->plan.groups.size();
+    std::vector<std::pair<int64_t, double>> seq;   // (term, angle)
+    for (auto &p : step_sequence(G, order))
+        for (int64_t j : ctx->plan.groups[p.first].terms) seq.push_back({j, p.second * dt * ctx->c[j]});
+    for (int64_t k = 0; k < steps; k++)
+        for (auto &t : seq)
+            CK(launch_pauli_rotation(dbl, d_state, ctx->n, ctx->x[t.first], ctx->z[t.first],
+                                     std::cos(t.second), std::sin(t.second), ctx->num_sms, st));
+    return SD_OK;
+}
+
+sd_status sd_expect(sd_ctx *ctx, const void *d_state, sd_dtype dtype, int64_t mo, const uint64_t *ox,
+                    const uint64_t *oz, const double *oc, double *out_host, void *cuda_stream) {
+    if (!out_host) return fail(ctx, SD_EINVAL, "null output pointer");
+    sd_status s = check_state_args(ctx, d_state, dtype, 1);
+    if (s != SD_OK) return s;
+    if ((s = check_obs(ctx, mo, ox, oz, oc)) != SD_OK) return s;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    StagedObs so;
+    if ((s = stage_obs(ctx, mo, ox, oz, oc, so)) != SD_OK) return s;
+    if ((s = ensure_partial(ctx, 1)) != SD_OK) return s;
+    if ((s = expect_async(ctx, d_state, dtype == SD_C128, so, ctx->d_scalar, st)) != SD_OK) return s;
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *out_host = v;
+    return SD_OK;
+}
+
+sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt, int64_t steps,
+                  int order, int64_t mo, const uint64_t *ox, const uint64_t *oz, const double *oc,
+                  double *value_out, double *grad_out, void *cuda_stream) {
+    sd_status s = check_state_args(ctx, d_state0, dtype, order);
+    if (s != SD_OK) return s;
+    if (!value_out || !grad_out) return fail(ctx, SD_EINVAL, "null output pointer");
+    if (steps < 0 || !std::isfinite(dt)) return fail(ctx, SD_EINVAL, "invalid steps or dt");
+    if (ctx->n < 4) return fail(ctx, SD_EINVAL, "sd_grad needs n >= 4");
+    if ((s = check_obs(ctx, mo, ox, oz, oc)) != SD_OK) return s;
+    const bool dbl = dtype == SD_C128;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t bytes = (size_t)(dbl ? 16 : 8) << ctx->n;
+    if (ctx->work_bytes < bytes) {
+        cudaFree(ctx->d_work[0]);
+        cudaFree(ctx->d_work[1]);
+        ctx->d_work[0] = ctx->d_work[1] = nullptr;
+        ctx->work_bytes = 0;
+        CK(cudaMalloc(&ctx->d_work[0], bytes));
+        CK(cudaMalloc(&ctx->d_work[1], bytes));
+        ctx->work_bytes = bytes;
+    }
+    if (!ctx->d_gacc) CK(cudaMalloc((void **)&ctx->d_gacc, sizeof(double) * std::max<int64_t>(ctx->m, 1)));
+    // gradient programs depend on dt: drop those made for another step size
+    if (!ctx->grad_groups.empty() && ctx->grad_dt != dt) {
+        for (void *a : ctx->grad_allocs) cudaFree(a);
+        ctx->grad_allocs.clear();
+        ctx->grad_groups.clear();
+    }
+    ctx->grad_dt = dt;
+    void *phi = ctx->d_work[0], *lam = ctx->d_work[1];
+    CK(cudaMemcpyAsync(phi, d_state0, bytes, cudaMemcpyDeviceToDevice, st));
+    if ((s = evolve_impl(ctx, phi, dbl, dt, steps, order, st)) != SD_OK) return s;
+    StagedObs so;
+    if ((s = stage_obs(ctx, mo, ox, oz, oc, so)) != SD_OK) return s;
+    if ((s = ensure_partial(ctx, 1)) != SD_OK) return s;
+    if ((s = expect_async(ctx, phi, dbl, so, ctx->d_scalar, st)) != SD_OK) return s;
+    const uint64_t *ax = staged_all_x(ctx, so);
+    CK(launch_apply_observable(dbl, phi, lam, ctx->n, ax, ax + mo,
+                               reinterpret_cast<const double *>(ax + 2 * mo), (int)mo, st));
+    CK(cudaMemsetAsync(ctx->d_gacc, 0, sizeof(double) * ctx->m, st));
+    const int G = (int)ctx->plan.groups.size();
+    const int blocks = grad_blocks(ctx->n, ctx->num_sms);
+    auto seq = step_sequence(G, order);
+    for (int64_t k = 0; k < steps; k++) {
+        for (auto it = seq.rbegin(); it != seq.rend(); ++it) {
+            const int g = it->first;
+            Program *cf = nullptr, *ci = nullptr;
+            GradGroup *gg = nullptr;
+            if ((s = get_cliff(ctx, dbl, g, true, cf)) != SD_OK) return s;
+            if ((s = get_cliff(ctx, dbl, g, false, ci)) != SD_OK) return s;
+            if ((s = get_grad_group(ctx, g, it->second, dt, gg)) != SD_OK) return s;
+            if ((s = ensure_partial(ctx, (size_t)blocks * std::max(gg->g.m, 1))) != SD_OK) return s;
+            if (!program_empty(*cf)) {
+                if ((s = run_program(ctx, dbl, *cf, phi, 1, st)) != SD_OK) return s;
+                if ((s = run_program(ctx, dbl, *cf, lam, 1, st)) != SD_OK) return s;
+            }
+            CK(launch_grad_diag(dbl, phi, lam, ctx->n, gg->g, gg->masks_f, gg->qinv, nullptr,
+                                ctx->d_partial, blocks, st));
+            CK(launch_grad_finalize(ctx->d_partial, blocks, gg->g.m, gg->term_id, gg->factor,
+                                    ctx->d_gacc, st));
+            if (!program_empty(*ci)) {
+                if ((s = run_program(ctx, dbl, *ci, phi, 1, st)) != SD_OK) return s;
+                if ((s = run_program(ctx, dbl, *ci, lam, 1, st)) != SD_OK) return s;
+            }
+        }
+    }
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(grad_out, ctx->d_gacc, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *value_out = v;
+    return SD_OK;
+}
+
+sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t count, sd_dtype dtype,
+                          double dt, int64_t steps, int order, void *cuda_stream) {
+    sd_ctx *ctx = nullptr;
+    if (!ctxs || !d_states || count < 0) return fail(nullptr, SD_EINVAL, "invalid batch arguments");
+    for (int64_t i = 0; i < count; i++) {
+        sd_status s = check_state_args(ctxs[i], d_states[i], dtype, order);
+        if (s != SD_OK) return s;
+    }
+    for (int64_t i = 0; i < count; i++) {
+        ctx = ctxs[i];
+        sd_status s = evolve_impl(ctx, d_states[i], dtype == SD_C128, dt, steps, order,
+                                  (cudaStream_t)cuda_stream);
+        if (s != SD_OK) return s;
+    }
+    return SD_OK;
+}
+
+const char *sd_last_error(const sd_ctx *ctx) {
+    if (ctx && !ctx->err.empty()) return ctx->err.c_str();
+    return g_last_error.c_str();
+}
+
+void sd_destroy(sd_ctx *ctx) { delete ctx; }
+
+}  // extern "C"

@@ -1,0 +1,484 @@
+// Circuit building (Eq. trotter_simul_diag: C_g, exp(-i Lambda_g dt), C_g^dag
+// per group, with the layer structure of Fig. clifford_block) and the pass
+// scheduler that packs the resulting op stream into tile passes over the
+// state vector.
+//
+// A pass streams the state once through HBM in tiles of 2^K amplitudes.  A
+// tile is the set of indices that agree on every bit outside K "tile
+// qubits"; the lowest c qubits are always tile qubits so that loads and
+// stores move whole 128-byte lines.  Inside a pass, a thread block holds a
+// tile with 16 amplitudes per thread; a "round" assigns 4 tile positions to
+// the thread's registers, 5 to the warp lanes and the rest to the warps.
+// One-qubit gates are applied in registers on register positions; diagonal
+// ops (S/CZ layers, group exponentials) apply in any round; a run of CNOTs
+// whose targets are tile qubits is a permutation of the tile applied while
+// the registers are written back to shared memory between rounds.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <set>
+
+#include "sd_internal.h"
+
+namespace sd {
+
+int64_t turns_q64(double t) {
+    double f = t - std::nearbyint(t);   // in [-0.5, 0.5]
+    if (f >= 0.5) f -= 1.0;
+    if (f < -0.5) f += 1.0;
+    // f * 2^64 lies in [-2^63, 2^63): exact split into two 32-bit halves.
+    double s = std::ldexp(f, 32);              // [-2^31, 2^31)
+    double hi = std::floor(s);
+    double lo = std::ldexp(s - hi, 32);        // [0, 2^32)
+    int64_t h = (int64_t)hi;
+    uint64_t l = (uint64_t)std::nearbyint(lo);
+    uint64_t v = ((uint64_t)h << 32) + l;      // wraps mod 2^64
+    return (int64_t)v;
+}
+
+uint32_t swizzle_col(int p, int c) {
+    if (p < c) return 1u << p;
+    uint32_t span = (1u << c) - 1u;
+    uint32_t s = 1u + (uint32_t)((p - c) % (int)span);
+    return (1u << p) | s;
+}
+
+namespace {
+
+void layers(const GroupPlan &gp, std::vector<Gate> &ua, std::vector<Gate> &cn,
+            std::vector<Gate> &scz, std::vector<Gate> &hb) {
+    for (size_t k = 0; k < gp.gates.size(); k++) {
+        switch (gp.stage[k]) {
+        case ST_PRE:
+        case ST_ALG2: ua.push_back(gp.gates[k]); break;
+        case ST_ALG3: cn.push_back(gp.gates[k]); break;
+        case ST_ALG4: scz.push_back(gp.gates[k]); break;
+        default: hb.push_back(gp.gates[k]); break;
+        }
+    }
+}
+
+int add_phase(Circuit &c, int n, const std::vector<Gate> &scz, bool inverse) {
+    if (scz.empty()) return -1;
+    PhaseLayer L;
+    L.adj.assign(n, 0);
+    L.up.assign(n, 0);
+    for (auto &g : scz) {
+        if (g.kind == G_S) {
+            if (inverse) L.sm ^= uint64_t(1) << g.a; else L.sp ^= uint64_t(1) << g.a;
+        } else {
+            int a = std::min(g.a, g.b), b = std::max(g.a, g.b);
+            L.adj[a] ^= uint64_t(1) << b;
+            L.adj[b] ^= uint64_t(1) << a;
+            L.up[a] ^= uint64_t(1) << b;
+        }
+    }
+    uint64_t sup = L.sp | L.sm;
+    for (int q = 0; q < n; q++)
+        if (L.adj[q]) sup |= uint64_t(1) << q;
+    if (sup == 0) return -1;
+    c.phases.push_back(L);
+    FlatOp op{OK_PHASE, -1, -1, (int32_t)c.phases.size() - 1, sup};
+    c.ops.push_back(op);
+    return (int)c.phases.size() - 1;
+}
+
+void add_1q(Circuit &c, const Gate &g, bool inverse) {
+    int32_t k = g.kind == G_H ? OK_H : (inverse ? OK_SDG : OK_S);
+    c.ops.push_back(FlatOp{k, g.a, -1, -1, uint64_t(1) << g.a});
+}
+
+void add_cnot(Circuit &c, const Gate &g) {
+    c.ops.push_back(FlatOp{OK_CNOT, g.a, g.b, -1, (uint64_t(1) << g.a) | (uint64_t(1) << g.b)});
+}
+
+}  // namespace
+
+void append_clifford(const Plan &plan, int g, bool forward, Circuit &c) {
+    std::vector<Gate> ua, cn, scz, hb;
+    layers(plan.groups[g], ua, cn, scz, hb);
+    if (forward) {
+        for (auto &x : ua) add_1q(c, x, false);
+        for (auto &x : cn) add_cnot(c, x);
+        add_phase(c, plan.n, scz, false);
+        for (auto &x : hb) add_1q(c, x, false);
+    } else {
+        for (auto it = hb.rbegin(); it != hb.rend(); ++it) add_1q(c, *it, true);
+        add_phase(c, plan.n, scz, true);
+        for (auto it = cn.rbegin(); it != cn.rend(); ++it) add_cnot(c, *it);
+        for (auto it = ua.rbegin(); it != ua.rend(); ++it) add_1q(c, *it, true);
+    }
+}
+
+void append_group_step(const Plan &plan, int g, double f, double dt,
+                       const std::vector<double> &coeffs, Circuit &c) {
+    const GroupPlan &gp = plan.groups[g];
+    append_clifford(plan, g, true, c);
+    DiagLayer D;
+    D.group = g;
+    D.frac = f;
+    uint64_t sup = 0;
+    const double inv2pi = 1.0 / (2.0 * M_PI);
+    for (size_t k = 0; k < gp.terms.size(); k++) {
+        double a = f * dt * coeffs[gp.terms[k]];
+        if (gp.signs[k]) a = -a;
+        D.masks.push_back(gp.masks[k]);
+        D.q.push_back(turns_q64(a * inv2pi));
+        sup |= gp.masks[k];
+    }
+    c.diags.push_back(std::move(D));
+    c.ops.push_back(FlatOp{OK_DIAG, -1, -1, (int32_t)c.diags.size() - 1, sup});
+    append_clifford(plan, g, false, c);
+}
+
+// ------------------------------------------------------------ scheduler
+
+namespace {
+
+struct SchedState {
+    const Circuit &circ;
+    int n, K, c;
+    std::vector<std::vector<int>> preds;
+    std::vector<int> done_round;  // -1 = not done; else global round id
+    std::vector<char> is_cnot;
+    explicit SchedState(const Circuit &cc) : circ(cc) {}
+};
+
+std::vector<int> wires_of(const FlatOp &op, int n) {
+    std::vector<int> w;
+    if (op.kind == OK_PHASE || op.kind == OK_DIAG) {
+        for (int q = 0; q < n; q++)
+            if ((op.support >> q) & 1) w.push_back(q);
+    } else {
+        w.push_back(op.q);
+        if (op.kind == OK_CNOT) w.push_back(op.q2);
+    }
+    return w;
+}
+
+int rank_cols(const std::vector<uint32_t> &cols, int c) {
+    std::vector<uint32_t> v;
+    for (auto x : cols) v.push_back(x & ((1u << c) - 1u));
+    int r = 0;
+    for (int b = 0; b < c; b++) {
+        int p = -1;
+        for (int i = r; i < (int)v.size(); i++)
+            if ((v[i] >> b) & 1) { p = i; break; }
+        if (p < 0) continue;
+        std::swap(v[r], v[p]);
+        for (int i = 0; i < (int)v.size(); i++)
+            if (i != r && ((v[i] >> b) & 1)) v[i] ^= v[r];
+        r++;
+    }
+    return r;
+}
+
+// Lane/warp assignment of the non-register tile positions.
+void assign_layout(DevRound &R, int K, int c, bool global_io) {
+    std::vector<int> rest;
+    for (int p = 0; p < K; p++) {
+        bool isreg = false;
+        for (int i = 0; i < 4; i++) isreg |= R.reg_pos[i] == p;
+        if (!isreg) rest.push_back(p);
+    }
+    std::vector<int> lanes;
+    if (global_io) {
+        for (int p = 0; p < c; p++) lanes.push_back(p);
+        for (int p : rest)
+            if ((int)lanes.size() < kLaneBits && p >= c) lanes.push_back(p);
+    } else {
+        std::vector<uint32_t> cols;
+        for (int p : rest) {
+            if ((int)lanes.size() >= kLaneBits) break;
+            std::vector<uint32_t> t = cols;
+            t.push_back(swizzle_col(p, c));
+            if (rank_cols(t, c) > rank_cols(cols, c)) {
+                lanes.push_back(p);
+                cols = t;
+            }
+        }
+        for (int p : rest)
+            if ((int)lanes.size() < kLaneBits &&
+                std::find(lanes.begin(), lanes.end(), p) == lanes.end())
+                lanes.push_back(p);
+    }
+    std::sort(lanes.begin(), lanes.end());
+    int li = 0, wi = 0;
+    for (int p : rest) {
+        if (std::find(lanes.begin(), lanes.end(), p) != lanes.end()) R.lane_pos[li++] = (uint8_t)p;
+        else R.warp_pos[wi++] = (uint8_t)p;
+    }
+    for (; wi < 7; wi++) R.warp_pos[wi] = 0xff;
+}
+
+}  // namespace
+
+std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &S) {
+    S = Schedule{};
+    S.K = K;
+    S.c = c;
+    if (K < kRegBits + kLaneBits || K > 13 || n < K) return "invalid tile size";
+    const int N = (int)circ.ops.size();
+    std::vector<std::vector<int>> preds(N);
+    {
+        std::vector<int> last_nd(n, -1);
+        std::vector<std::vector<int>> diag_since(n);
+        for (int j = 0; j < N; j++) {
+            const FlatOp &op = circ.ops[j];
+            bool isdiag = op.kind == OK_PHASE || op.kind == OK_DIAG;
+            std::set<int> p;
+            for (int w : wires_of(op, n)) {
+                if (last_nd[w] >= 0) p.insert(last_nd[w]);
+                if (!isdiag)
+                    for (int d : diag_since[w]) p.insert(d);
+            }
+            preds[j].assign(p.begin(), p.end());
+            for (int w : wires_of(op, n)) {
+                if (isdiag) diag_since[w].push_back(j);
+                else { last_nd[w] = j; diag_since[w].clear(); }
+            }
+        }
+    }
+    std::vector<int> done(N, -1);   // global round id in which the op ran
+    int round_id = 0;
+    int first = 0;
+    std::map<std::pair<int, int>, int64_t> adj_base;  // phase idx -> pool bases
+    auto ensure_phase_pool = [&](int idx) {
+        auto key = std::make_pair(idx, 0);
+        auto it = adj_base.find(key);
+        if (it != adj_base.end()) return it->second;
+        int64_t b = (int64_t)S.mask_pool.size();
+        const PhaseLayer &L = circ.phases[idx];
+        for (int q = 0; q < n; q++) S.mask_pool.push_back(L.adj[q]);
+        for (int q = 0; q < n; q++) S.mask_pool.push_back(L.up[q]);
+        adj_base[key] = b;
+        return b;
+    };
+
+    int guard = 0;
+    while (first < N) {
+        if (++guard > 4 * N + 16) return "scheduler made no progress";
+        // -------- choose the tile qubits
+        std::vector<int> need(n, INT32_MAX);
+        for (int j = first; j < N; j++) {
+            if (done[j] >= 0) continue;
+            const FlatOp &op = circ.ops[j];
+            int q = -1;
+            if (op.kind == OK_H || op.kind == OK_S || op.kind == OK_SDG) q = op.q;
+            else if (op.kind == OK_CNOT) q = op.q2;
+            if (q >= 0 && need[q] == INT32_MAX) need[q] = j;
+        }
+        std::vector<int> cand;
+        for (int q = c; q < n; q++) cand.push_back(q);
+        std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return need[a] < need[b]; });
+        std::vector<int> tq;
+        for (int q = 0; q < c; q++) tq.push_back(q);
+        std::vector<int> hi(cand.begin(), cand.begin() + (K - c));
+        std::sort(hi.begin(), hi.end());
+        for (int q : hi) tq.push_back(q);
+        int pos_of[64];
+        for (int q = 0; q < 64; q++) pos_of[q] = -1;
+        for (int p = 0; p < K; p++) pos_of[tq[p]] = p;
+
+        DevPass P{};
+        P.round_begin = (int)S.rounds.size();
+        for (int p = 0; p < K; p++) P.tile_bits[p] = (uint8_t)tq[p];
+        int no = 0;
+        for (int q = 0; q < n; q++)
+            if (pos_of[q] < 0) P.outer_bits[no++] = (uint8_t)q;
+        P.n_outer = no;
+        int h_count = 0;
+        int diag_op_index = -1;
+
+        int nr = 0;
+        for (;;) {
+            bool is_load = nr == 0;
+            // -------- register positions for this round
+            std::vector<std::pair<int, int>> score;  // (first pending G1 index, position)
+            for (int p = 0; p < K; p++) {
+                if (is_load && p < c) continue;
+                int best = INT32_MAX;
+                for (int j = first; j < N; j++) {
+                    if (done[j] >= 0) continue;
+                    const FlatOp &op = circ.ops[j];
+                    if ((op.kind == OK_H || op.kind == OK_S || op.kind == OK_SDG) && op.q == tq[p]) {
+                        best = j;
+                        break;
+                    }
+                }
+                score.push_back({best, p});
+            }
+            std::stable_sort(score.begin(), score.end());
+            DevRound R{};
+            std::vector<int> regs;
+            for (int i = 0; i < 4; i++) regs.push_back(score[i].second);
+            std::sort(regs.begin(), regs.end());
+            for (int i = 0; i < 4; i++) R.reg_pos[i] = (uint8_t)regs[i];
+            R.perm = -1;
+            R.flags = is_load ? 1 : 0;
+            R.op_begin = (int)S.ops.size();
+            // -------- execute what is ready
+            std::vector<Gate> perm_cnots;
+            int executed = 0;
+            bool progress = true;
+            while (progress) {
+                progress = false;
+                for (int j = first; j < N; j++) {
+                    if (done[j] >= 0) continue;
+                    const FlatOp &op = circ.ops[j];
+                    bool ok = true;
+                    for (int p : preds[j]) {
+                        if (done[p] < 0) { ok = false; break; }
+                        // ops after a CNOT of this round's permutation wait for the next round
+                        if (done[p] == round_id && circ.ops[p].kind == OK_CNOT && op.kind != OK_CNOT) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (!ok) continue;
+                    int slot = -1;
+                    if (op.kind == OK_H || op.kind == OK_S || op.kind == OK_SDG) {
+                        int p = pos_of[op.q];
+                        if (p < 0) continue;
+                        for (int i = 0; i < 4; i++)
+                            if (R.reg_pos[i] == p) slot = i;
+                        if (slot < 0) continue;
+                        if (!perm_cnots.empty()) {
+                            // a 1q gate sharing a wire with a queued CNOT must precede it
+                            bool clash = false;
+                            for (auto &g : perm_cnots) clash |= g.a == op.q || g.b == op.q;
+                            if (clash) continue;
+                        }
+                        DevOp d{op.kind == OK_H ? D_H : (op.kind == OK_S ? D_S : D_SDG), slot, 0, 0};
+                        S.ops.push_back(d);
+                        if (op.kind == OK_H) h_count++;
+                    } else if (op.kind == OK_CNOT) {
+                        if (pos_of[op.q2] < 0) continue;
+                        perm_cnots.push_back(Gate{G_CNOT, op.q, op.q2});
+                    } else if (op.kind == OK_PHASE) {
+                        if (!perm_cnots.empty()) {
+                            bool clash = false;
+                            for (auto &g : perm_cnots)
+                                clash |= ((op.support >> g.a) & 1) || ((op.support >> g.b) & 1);
+                            if (clash) continue;
+                        }
+                        const PhaseLayer &L = circ.phases[op.idx];
+                        DevPhase ph{};
+                        ph.sp = L.sp;
+                        ph.sm = L.sm;
+                        int64_t b = ensure_phase_pool(op.idx);
+                        ph.adj_base = b;
+                        ph.up_base = b + n;
+                        ph.n = n;
+                        for (int i = 0; i < 4; i++) {
+                            int qi = tq[R.reg_pos[i]];
+                            ph.lin_s[i] = ((L.sp >> qi) & 1) ? 1 : (((L.sm >> qi) & 1) ? -1 : 0);
+                        }
+                        ph.quad = 0;
+                        for (int i = 0; i < 4; i++)
+                            for (int k = i + 1; k < 4; k++) {
+                                int qi = tq[R.reg_pos[i]], qk = tq[R.reg_pos[k]];
+                                if ((L.adj[qi] >> qk) & 1) ph.quad |= 1 << (i * 4 + k);
+                            }
+                        S.phases.push_back(ph);
+                        S.ops.push_back(DevOp{D_PHASE, 0, (int32_t)S.phases.size() - 1, 0});
+                    } else {  // OK_DIAG
+                        if (!perm_cnots.empty()) {
+                            bool clash = false;
+                            for (auto &g : perm_cnots)
+                                clash |= ((op.support >> g.a) & 1) || ((op.support >> g.b) & 1);
+                            if (clash) continue;
+                        }
+                        const DiagLayer &D = circ.diags[op.idx];
+                        uint64_t regmask = 0;
+                        int gq[4];
+                        for (int i = 0; i < 4; i++) {
+                            gq[i] = tq[R.reg_pos[i]];
+                            regmask |= uint64_t(1) << gq[i];
+                        }
+                        std::vector<std::vector<int>> cls(16);
+                        for (size_t t = 0; t < D.masks.size(); t++) {
+                            int u = 0;
+                            for (int i = 0; i < 4; i++) u |= int((D.masks[t] >> gq[i]) & 1) << i;
+                            cls[u].push_back((int)t);
+                        }
+                        DevDiag dd{};
+                        dd.base = (int64_t)S.term_q.size();
+                        int off = 0;
+                        for (int s = 0; s < 16; s++) {
+                            dd.off[s] = off;
+                            for (int t : cls[s]) {
+                                S.term_masks.push_back(D.masks[t] & ~regmask);
+                                S.term_q.push_back(D.q[t]);
+                                off++;
+                            }
+                        }
+                        dd.off[16] = off;
+                        S.diags.push_back(dd);
+                        S.ops.push_back(DevOp{D_DIAG, 0, (int32_t)S.diags.size() - 1, 0});
+                        if (diag_op_index < 0) diag_op_index = (int)S.ops.size() - 1;
+                    }
+                    done[j] = round_id;
+                    executed++;
+                    progress = true;
+                }
+            }
+            while (first < N && done[first] >= 0) first++;
+            R.op_end = (int)S.ops.size();
+            if (!perm_cnots.empty()) {
+                DevPerm pm{};
+                for (int p = 0; p < K; p++) {
+                    uint64_t v = uint64_t(1) << tq[p];
+                    for (auto &g : perm_cnots) v ^= ((v >> g.a) & 1) << g.b;
+                    uint32_t l = 0;
+                    for (int p2 = 0; p2 < K; p2++) l |= uint32_t((v >> tq[p2]) & 1) << p2;
+                    pm.col[p] = l;
+                }
+                for (int k = 0; k < no; k++) {
+                    uint64_t v = uint64_t(1) << P.outer_bits[k];
+                    for (auto &g : perm_cnots) v ^= ((v >> g.a) & 1) << g.b;
+                    uint32_t l = 0;
+                    for (int p2 = 0; p2 < K; p2++) l |= uint32_t((v >> tq[p2]) & 1) << p2;
+                    pm.ocol[k] = l;
+                }
+                S.perms.push_back(pm);
+                R.perm = (int)S.perms.size() - 1;
+            }
+            bool useful = executed > 0 || is_load;
+            if (!useful) break;
+            S.rounds.push_back(R);
+            nr++;
+            round_id++;
+            if (first >= N || nr >= 8) break;
+        }
+        // -------- the last round stores to global memory
+        DevRound &last = S.rounds.back();
+        bool store_ok = last.perm < 0;
+        for (int i = 0; i < 4; i++) store_ok &= last.reg_pos[i] >= c;
+        if (!store_ok) {
+            DevRound R{};
+            // register positions: the 4 lowest positions >= c
+            for (int i = 0; i < 4; i++) R.reg_pos[i] = (uint8_t)(c + i);
+            R.perm = -1;
+            R.op_begin = R.op_end = (int)S.ops.size();
+            R.flags = 0;
+            S.rounds.push_back(R);
+            nr++;
+            round_id++;
+        }
+        S.rounds.back().flags |= 2;
+        for (int r = P.round_begin; r < (int)S.rounds.size(); r++)
+            assign_layout(S.rounds[r], K, c, (S.rounds[r].flags & 3) != 0);
+        P.n_rounds = (int)S.rounds.size() - P.round_begin;
+        P.scale = std::ldexp(1.0, -(h_count / 2)) * ((h_count & 1) ? std::sqrt(0.5) : 1.0);
+        if (diag_op_index >= 0) {
+            P.scale_in_diag = 1;
+            S.ops[diag_op_index].pad = 1;
+            S.diag_passes++;
+        }
+        S.passes.push_back(P);
+    }
+    return "";
+}
+
+}  // namespace sd

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: ||psi_gpu - psi_oracle||_2 <= 1e-10 for complex128 states and
+<= 1e-4 for complex64 states (both with the oracle in complex128).  The
+oracle applies one rotation at a time in group order; the GPU applies whole
+groups through their Clifford frames, so agreement is up to rounding only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import planner as P
+from workloads import (from_strings, heisenberg_lattice, jw_like, neel_index, random_klocal,
+                       tfim_chain, basis_state, plus_state, product_state, haar_product_factors,
+                       gradient_2local, z_average_observable, batch_instances)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "c64": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def sd():
+    import torch
+    import paper_2206_11664_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def _dev(psi, dt):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(psi)).to(torch.complex128 if dt == "c128" else torch.complex64)
+    return t.cuda()
+
+
+def _host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def _rand_state(rng, n):
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return v / np.linalg.norm(v)
+
+
+def _check(sd, h, psi0, dt_, steps, order, dtype, skip_rule=-1, tile_bits=0, pauli=False):
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(skip_rule=skip_rule, tile_bits=tile_bits)
+    groups = P.greedy_partition(h.x, h.z)
+    ref = oracle.evolve(h, psi0, dt_, steps, order, groups)
+    t = _dev(psi0, dtype)
+    if pauli:
+        sim.evolve_pauli(t, dt_, steps, order)
+    else:
+        sim.evolve(t, dt_, steps, order)
+    err = np.linalg.norm(_host(t) - ref)
+    assert err <= TOL[dtype], (h.n, dtype, order, err)
+    return err
+
+
+# ---------------------------------------------------------------- on-chip path (small n)
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_small_random(sd, dtype, order):
+    rng = np.random.default_rng(100 + order)
+    for n in (1, 2, 3, 5, 8, 11):
+        h = random_klocal(n, 3 * n + 4, rng, weights=tuple(w for w in (1, 2, 3, 4) if w <= n))
+        _check(sd, h, _rand_state(rng, n), 0.07, 5, order, dtype)
+
+
+def test_worked_example_group(sd):
+    ex = ["YIXI", "IXIY", "XZYZ", "YZXZ", "XIYI", "IYIX", "ZXZY", "ZYZX"]
+    rng = np.random.default_rng(3)
+    h = from_strings(ex, rng.uniform(-1, 1, 8))
+    for rule in (0, 1, 2):
+        _check(sd, h, _rand_state(rng, 4), 0.2, 3, 1, "c128", skip_rule=rule)
+
+
+def test_tfim_chain_config(sd):
+    """TFIM open chain n=10, J=1, h=0.9, |0..0>, dt=0.01, 100 first-order steps,
+    complex128, <Z_0> after every step."""
+    import torch
+    h = tfim_chain(10)
+    psi0 = basis_state(10, 0)
+    err = _check(sd, h, psi0, 0.01, 100, 1, "c128")
+    assert err < 1e-12
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    t = _dev(psi0, "c128")
+    obs = (np.array([0], np.uint64), np.array([1], np.uint64), np.array([1.0]))
+    trace = torch.zeros(100, dtype=torch.float64, device="cuda")
+    sim.evolve_observe(t, 0.01, 100, obs, trace)
+    tr = trace.cpu().numpy()
+    groups = P.greedy_partition(h.x, h.z)
+    st = psi0
+    ref = []
+    for k in range(100):
+        st = oracle.evolve(h, st, 0.01, 1, 1, groups)
+        ref.append(oracle.expect(st, *obs))
+    assert np.max(np.abs(tr - np.array(ref))) < 1e-12
+
+
+# ---------------------------------------------------------------- tile path (several tiles)
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("rule", [0, 2])
+def test_tile_random_klocal(sd, dtype, rule):
+    rng = np.random.default_rng(7 + rule)
+    for n in (14, 16):
+        h = random_klocal(n, 60, rng, weights=(2, 3, 4))
+        _check(sd, h, _rand_state(rng, n), 0.05, 2, 2, dtype, skip_rule=rule)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("K", [9, 10, 11, 12, 13])
+def test_tile_sizes(sd, dtype, K):
+    rng = np.random.default_rng(K)
+    n = 15
+    h = random_klocal(n, 40, rng, weights=(1, 2, 3))
+    _check(sd, h, _rand_state(rng, n), 0.1, 2, 1, dtype, tile_bits=K)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_tile_heisenberg_lattice(sd, dtype):
+    h = heisenberg_lattice(4, 4)
+    psi0 = basis_state(16, neel_index(4, 4))
+    for rule in (0, 1, 2):
+        _check(sd, h, psi0, 0.02, 10, 1, dtype, skip_rule=rule)
+
+
+def test_tile_jw_like(sd):
+    rng = np.random.default_rng(5)
+    h = jw_like(n=15, m=600, rng=rng)
+    psi0 = basis_state(15, (1 << 7) - 1)
+    _check(sd, h, psi0, 0.05, 3, 2, "c128")
+    _check(sd, h, psi0, 0.05, 3, 2, "c64")
+
+
+def test_tile_gradient_hamiltonian_plus_state(sd):
+    rng = np.random.default_rng(6)
+    h = gradient_2local(n=16, m=80, rng=rng)
+    _check(sd, h, plus_state(16), 0.01, 5, 1, "c128")
+
+
+def test_identity_and_single_terms(sd):
+    h = from_strings(["IIIIIIIIIIIIII", "XIIIIIIIIIIIII", "IIIIIIIIIIIIIZ", "YYYYYYYYYYYYYY"],
+                     [0.3, -0.7, 1.1, 0.4])
+    rng = np.random.default_rng(9)
+    _check(sd, h, _rand_state(rng, 14), 0.3, 4, 2, "c128")
+
+
+# ---------------------------------------------------------------- baseline path
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_per_pauli_path(sd, dtype):
+    rng = np.random.default_rng(21)
+    for n in (6, 15):
+        h = random_klocal(n, 30, rng, weights=(1, 2, 3))
+        _check(sd, h, _rand_state(rng, n), 0.05, 2, 2, dtype, pauli=True)
+
+
+# ---------------------------------------------------------------- expectation, gradient, batch
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_expectation(sd, dtype):
+    rng = np.random.default_rng(31)
+    for n in (5, 15):
+        h = random_klocal(n, 20, rng, weights=(1, 2, 3))
+        psi = _rand_state(rng, n)
+        sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+        got = sim.expect(_dev(psi, dtype), (h.x, h.z, h.c))
+        ref = oracle.expect(psi, h.x, h.z, h.c)
+        assert abs(got - ref) < (1e-12 if dtype == "c128" else 1e-5) * max(1, abs(ref))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("n", [6, 14])
+def test_gradient_vs_oracle(sd, order, n):
+    rng = np.random.default_rng(50 + n + order)
+    h = gradient_2local(n=n, m=24, rng=rng)
+    psi0 = plus_state(n)
+    obs = z_average_observable(n)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    t = _dev(psi0, "c128")
+    f, g = sim.grad(t, 0.05, 4, obs, order)
+    f_ref, g_ref = oracle.grad(h, psi0, 0.05, 4, order, obs)
+    assert abs(f - f_ref) < 1e-12
+    assert np.max(np.abs(g - g_ref)) < 1e-9 * max(1.0, np.max(np.abs(g_ref)))
+    assert np.allclose(_host(t), psi0)   # state0 untouched
+
+
+def test_gradient_autograd_function(sd):
+    import torch
+    rng = np.random.default_rng(77)
+    n = 8
+    h = gradient_2local(n=n, m=12, rng=rng)
+    obs = z_average_observable(n)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    t = _dev(plus_state(n), "c128")
+    c = torch.tensor(h.c, dtype=torch.float64, requires_grad=True)
+    f = sd.TrotterExpectation.apply(c, sim, t, 0.05, 3, obs, 1)
+    f.backward()
+    _, g_ref = oracle.grad(h, plus_state(n), 0.05, 3, 1, obs)
+    assert np.max(np.abs(c.grad.numpy() - g_ref)) < 1e-9
+
+
+def test_batch_matches_individual(sd):
+    rng = np.random.default_rng(90)
+    sims, states, refs = [], [], []
+    for i in range(4):
+        n = int(rng.integers(9, 15))
+        h = random_klocal(n, 40, rng)
+        psi = product_state(haar_product_factors(n, rng))
+        sims.append(sd.Simulator(h.n, h.x, h.z, h.c).plan())
+        states.append(_dev(psi, "c64"))
+        refs.append(oracle.evolve(h, psi, 0.005, 3, 2))
+    sd.evolve_batch(sims, states, 0.005, 3, 2)
+    for t, r in zip(states, refs):
+        assert np.linalg.norm(_host(t) - r) < 1e-4
+
+
+def test_invalid_state_rejected(sd):
+    import torch
+    h = tfim_chain(10)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    with pytest.raises(TypeError):
+        sim.evolve(torch.zeros(1024, dtype=torch.complex64), 0.1, 1)
+    with pytest.raises(sd.SDError):
+        sim.evolve(torch.zeros(1024, dtype=torch.complex64, device="cuda"), 0.1, 1, order=3)

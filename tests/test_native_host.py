@@ -1,0 +1,136 @@
+"""Host-side tests of the native library (no GPU needed).
+
+The library loads and exports every symbol of include/sd.h; its planner
+(C++) agrees bit for bit with the independent oracle planner (Python) on
+groups, gate lists, masks, signs and CNOT index maps; argument validation
+returns the documented status codes; the pass scheduler covers every op.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import planner as P
+from workloads import (batch_instances, from_strings, gradient_2local, heisenberg_lattice,
+                       jw_like, random_klocal, tfim_chain)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sd():
+    from paper_2206_11664_gb300 import build
+    build.build()
+    import paper_2206_11664_gb300 as m
+    return m
+
+
+def test_exports_every_declared_symbol(sd):
+    from paper_2206_11664_gb300 import _native
+    lib = _native.load()
+    hdr = open(os.path.join(ROOT, "include", "sd.h")).read()
+    names = set(re.findall(r"\b(sd_[a-z_]+)\s*\(", hdr))
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _native.SIGNATURES, name
+
+
+KIND = {"H": 0, "S": 1, "CNOT": 2, "CZ": 3}
+
+
+def _compare(sd, h, rule):
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(skip_rule=rule)
+    v = sim.plan_view()
+    pl = P.plan(h.n, h.x, h.z, skip_rule=rule)
+    G = v["n_groups"]
+    assert G == len(pl.groups)
+    for g in range(G):
+        a, b = v["group_offsets"][g], v["group_offsets"][g + 1]
+        assert v["group_terms"][a:b].tolist() == pl.groups[g]
+        assert v["masks"][a:b].tolist() == pl.masks[g]
+        assert v["signs"][a:b].tolist() == pl.signs[g]
+        ga, gb = v["gate_offsets"][g], v["gate_offsets"][g + 1]
+        assert v["gates"][ga:gb].tolist() == [[KIND[k], x, y] for k, x, y in pl.gates[g]]
+        A, Ai = P.cnot_layer_matrix(pl.gates[g], h.n)
+        assert v["cnot_cols"][g].tolist() == A
+        assert v["cnot_inv_cols"][g].tolist() == Ai
+    return sim
+
+
+def test_worked_example_through_abi(sd):
+    ex = ["YIXI", "IXIY", "XZYZ", "YZXZ", "XIYI", "IYIX", "ZXZY", "ZYZX"]
+    h = from_strings(ex, np.ones(8))
+    for rule in (0, 1, 2):
+        _compare(sd, h, rule)
+
+
+@pytest.mark.parametrize("name", ["tfim", "heis30", "heis32", "grad", "jw"])
+def test_planner_bit_exact_on_workloads(sd, name):
+    h = {"tfim": lambda: tfim_chain(10), "heis30": lambda: heisenberg_lattice(5, 6),
+         "heis32": lambda: heisenberg_lattice(6, 6, drop_corners=True),
+         "grad": gradient_2local, "jw": jw_like}[name]()
+    _compare(sd, h, 2)
+
+
+def test_planner_bit_exact_on_batch_instances(sd):
+    for h, _ in batch_instances(3):
+        _compare(sd, h, 2)
+
+
+@pytest.mark.parametrize("rule", [0, 1, 2])
+def test_planner_bit_exact_random(sd, rule):
+    rng = np.random.default_rng(40 + rule)
+    for _ in range(30):
+        n = int(rng.integers(3, 12))
+        h = random_klocal(n, int(rng.integers(5, 60)), rng, weights=tuple(w for w in (1, 2, 3, 4) if w <= n))
+        _compare(sd, h, rule)
+
+
+def test_argument_validation(sd):
+    from paper_2206_11664_gb300 import _native as N
+    lib = N.load()
+    h = ctypes.c_void_p()
+    x = np.array([1 << 5], np.uint64)
+    z = np.array([0], np.uint64)
+    c = np.array([1.0])
+    P64 = ctypes.POINTER(ctypes.c_uint64)
+    PD = ctypes.POINTER(ctypes.c_double)
+    st = lib.sd_create(3, 1, x.ctypes.data_as(P64), z.ctypes.data_as(P64), c.ctypes.data_as(PD),
+                       ctypes.byref(h))
+    assert st == N.SD_EINVAL and b"mask bit" in lib.sd_last_error(None)
+    st = lib.sd_create(0, 1, x.ctypes.data_as(P64), z.ctypes.data_as(P64), c.ctypes.data_as(PD),
+                       ctypes.byref(h))
+    assert st == N.SD_EINVAL
+    with pytest.raises(sd.SDError):
+        sd.Simulator.from_strings(["XQ"], [1.0])
+    sim = sd.Simulator.from_strings(["XX", "ZZ"], [1.0, 2.0])
+    v = N.PlanView()
+    assert lib.sd_get_plan(sim._h, ctypes.byref(v)) == N.SD_ENOPLAN
+    with pytest.raises(sd.SDError):
+        sim.plan(skip_rule=7)
+    with pytest.raises(sd.SDError):
+        sim.plan(tile_bits=20)
+    sim.plan()
+    assert sim.plan_view()["n_groups"] == 1
+    c_bad = np.array([np.nan, 1.0])
+    with pytest.raises(sd.SDError):
+        sim.set_coeffs(c_bad)
+
+
+def test_schedule_covers_heisenberg_step(sd):
+    h = heisenberg_lattice(5, 6)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    s64 = sim.schedule_stats(sd.C64, 1)
+    s128 = sim.schedule_stats(sd.C128, 1)
+    # three group exponentials per step, far fewer passes than the 147 terms
+    assert s64["diag_passes"] == 3 and s64["passes_per_step"] <= 10
+    assert s128["passes_per_step"] <= 14
+
+
+def test_schedule_stats_small_state_is_onchip(sd):
+    t = tfim_chain(10)
+    sim = sd.Simulator(t.n, t.x, t.z, t.c).plan()
+    assert sim.schedule_stats(sd.C128, 1)["onchip"]
