@@ -72,7 +72,13 @@ typedef struct {
     /* Tile size of the state-vector passes, log2 amplitudes per CTA tile:
      * 0 = chosen by the autotuner, else 9..13. */
     int tile_bits;
-    int reserved[6];
+    /* Run-time specialisation of the tile passes (each pass compiled with
+     * NVRTC for sm_103a, cached in memory and under $SD_JIT_CACHE or
+     * ~/.cache/sd_jit): 0 = automatic (states of 20+ qubits with at most 128
+     * passes per program), 1 = always on the tile path, -1 = never.  Falls
+     * back to the precompiled interpreter kernel if NVRTC is unavailable. */
+    int jit;
+    int reserved[5];
 } sd_plan_opts;
 
 /* Read-only view of a plan; pointers stay valid until the next sd_plan or

@@ -116,8 +116,9 @@ class Simulator:
             pass
 
     # ------------------------------------------------------------ planning
-    def plan(self, skip_rule=-1, tile_bits=0):
-        o = N.PlanOpts(skip_rule, tile_bits)
+    def plan(self, skip_rule=-1, tile_bits=0, jit=0):
+        """Host planning.  jit: 0 automatic, 1 always, -1 never (see sd.h)."""
+        o = N.PlanOpts(skip_rule, tile_bits, jit)
         self._check(self._lib.sd_plan(self._h, ctypes.byref(o)))
         return self
 

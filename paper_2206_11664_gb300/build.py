@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsd.so")
-SOURCES = ["planner.cpp", "schedule.cpp", "api.cpp", "kernels.cu"]
+SOURCES = ["planner.cpp", "schedule.cpp", "api.cpp", "jit.cpp", "kernels.cu"]
+JIT_HEADERS = [("kJitDevTypes", "dev_types.h"), ("kJitTileDevice", "tile_device.cuh")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -27,9 +28,25 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def _embed_headers() -> None:
+    """Write _build/jit_headers.inc: the device headers the run-time compiler
+    needs, as C++ raw string literals."""
+    out = []
+    for var, name in JIT_HEADERS:
+        text = open(os.path.join(CSRC, name)).read()
+        assert ")SDJITSRC" not in text
+        out.append(f'static const char *{var} = R"SDJITSRC({text})SDJITSRC";\n')
+    path = os.path.join(OUT, "jit_headers.inc")
+    body = "".join(out)
+    if not os.path.exists(path) or open(path).read() != body:
+        with open(path, "w") as f:
+            f.write(body)
+
+
 def _compile(src: str, obj: str, verbose_ptxas: bool) -> None:
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-O2", "-I", os.path.join(HERE, "..", "include"), "-c", src, "-o", obj]
+           "-Xcompiler", "-O2", "-I", os.path.join(HERE, "..", "include"), "-I", OUT,
+           "-c", src, "-o", obj]
     if verbose_ptxas and src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-v"]
     subprocess.check_call(cmd)
@@ -49,13 +66,14 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     objs = [os.path.join(OUT, os.path.splitext(s)[0] + ".o") for s in SOURCES]
     if not force and not _stale(objs):
         return LIB
+    _embed_headers()
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         futs = [ex.submit(_compile, os.path.join(CSRC, s), o, verbose_ptxas)
                 for s, o in zip(SOURCES, objs)]
         for f in futs:
             f.result()
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+    subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

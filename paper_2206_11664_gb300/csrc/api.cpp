@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/sd.h"
+#include "jit.h"
 #include "kernels.cuh"
 #include "sd_internal.h"
 
@@ -28,6 +29,7 @@ thread_local std::string g_last_error;
 struct Program {
     bool onchip = false;
     DevSchedule sched;
+    JitProgram jit;           // run-time specialised passes, if built
     DevCircuit circ;
     std::vector<void *> allocs;
     int64_t passes = 0, rounds = 0, diag_passes = 0;
@@ -56,6 +58,8 @@ struct sd_ctx {
     bool planned = false;
     Plan plan;
     int tile_bits_opt = 0;
+    int jit_opt = 0;
+    std::string jit_note;    // why the last program did not use run-time specialisation
     // plan view storage
     std::vector<int64_t> v_goff, v_gterms, v_gateoff;
     std::vector<uint64_t> v_masks, v_cols, v_icols;
@@ -132,8 +136,10 @@ int default_tile_bits(const sd_ctx *ctx, bool dbl) {
 bool use_onchip(const sd_ctx *ctx, bool dbl) { return ctx->n <= onchip_max_qubits(dbl); }
 
 // Build and upload a program for a circuit.
-sd_status build_program(sd_ctx *ctx, const Circuit &circ, bool dbl, Program &P) {
+sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &P) {
     P.onchip = use_onchip(ctx, dbl);
+    Circuit circ = circ_in;
+    canonicalize_1q(circ, ctx->n);
     const int n = ctx->n;
     if (P.onchip) {
         std::vector<DevFlatOp> ops;
@@ -167,8 +173,16 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ, bool dbl, Program &P) 
     Schedule S;
     int K = default_tile_bits(ctx, dbl);
     int c = dbl ? 3 : 4;
-    std::string e = schedule_circuit(circ, n, K, c, S);
-    if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
+    for (;;) {
+        std::string e = schedule_circuit(circ, n, K, c, S);
+        if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
+        int ms = 0;
+        for (auto &p : S.passes) ms = std::max(ms, p.max_stage);
+        if (tile_pass_smem(dbl, K, ms) <= tile_pass_smem_limit()) break;
+        if (K <= kRegBits + kLaneBits)
+            return fail(ctx, SD_EINVAL, "a commuting group has too many terms for one tile pass");
+        K--;   // smaller tiles leave room to stage the group's terms
+    }
     DevSchedule &D = P.sched;
     D.K = S.K;
     D.c = S.c;
@@ -180,12 +194,23 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ, bool dbl, Program &P) 
     CK(upload(P.allocs, D.perms, S.perms));
     CK(upload(P.allocs, D.diags, S.diags));
     CK(upload(P.allocs, D.phases, S.phases));
-    CK(upload(P.allocs, D.term_masks, S.term_masks));
+    CK(upload(P.allocs, D.term_mo, S.term_mo));
+    CK(upload(P.allocs, D.term_ml, S.term_ml));
     CK(upload(P.allocs, D.term_q, S.term_q));
     CK(upload(P.allocs, D.mask_pool, S.mask_pool));
     P.passes = (int64_t)S.passes.size();
     P.rounds = (int64_t)S.rounds.size();
     P.diag_passes = S.diag_passes;
+    int mode = ctx->jit_opt;
+    if (const char *e = getenv("SD_JIT")) mode = atoi(e) > 0 ? 1 : (e[0] == '0' ? -1 : mode);
+    const bool want = mode > 0 || (mode == 0 && n >= 20 && P.passes <= 128);
+    if (want && P.passes > 0) {
+        std::string why = jit_build(S, n, dbl, P.jit);
+        if (!why.empty()) {
+            P.jit = JitProgram{};
+            ctx->jit_note = why;
+        }
+    }
     return SD_OK;
 }
 
@@ -258,6 +283,15 @@ sd_status run_program(sd_ctx *ctx, bool dbl, Program &P, void *psi, int64_t reps
     if (P.onchip) {
         if (P.circ.n_ops == 0 && nobs == 0) return SD_OK;
         CK(launch_onchip(dbl, psi, ctx->n, P.circ, reps, d_oz, d_oc, nobs, d_trace, st));
+        return SD_OK;
+    }
+    if (P.jit.ok()) {
+        const KParams kp{P.sched.passes, P.sched.rounds, P.sched.ops, P.sched.perms, P.sched.diags,
+                         P.sched.phases, P.sched.term_mo, P.sched.term_ml, P.sched.term_q,
+                         P.sched.mask_pool, P.sched.c};
+        for (int64_t r = 0; r < reps; r++)
+            for (int64_t p = 0; p < P.sched.n_passes; p++)
+                CK(jit_launch(P.jit, (int)p, psi, kp, ctx->n, ctx->num_sms, st));
         return SD_OK;
     }
     for (int64_t r = 0; r < reps; r++)
@@ -541,10 +575,11 @@ sd_status sd_set_coeffs(sd_ctx *ctx, const double *coeffs) {
 
 sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
-    int rule = 2, tb = 0;
+    int rule = 2, tb = 0, jit = 0;
     if (opts) {
         rule = opts->skip_rule < 0 ? 2 : opts->skip_rule;
         tb = opts->tile_bits;
+        jit = opts->jit;
         if (rule > 2) return fail(ctx, SD_EINVAL, "skip_rule must be -1, 0, 1 or 2");
         if (tb != 0 && (tb < 9 || tb > 13)) return fail(ctx, SD_EINVAL, "tile_bits must be 0 or 9..13");
     }
@@ -560,6 +595,7 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     ctx->grad_groups.clear();
     ctx->plan = std::move(p);
     ctx->tile_bits_opt = tb;
+    ctx->jit_opt = jit;
     ctx->planned = true;
     // plan view
     const int n = ctx->n;
@@ -618,6 +654,7 @@ sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_st
     if (out->onchip) return SD_OK;
     const int G = (int)ctx->plan.groups.size();
     Circuit c = segment_circuit(ctx, order, (order == 2 && G > 1) ? 2 : 0, 0.01);
+    canonicalize_1q(c, ctx->n);
     Schedule S;
     int K = default_tile_bits(ctx, dbl);
     std::string e = schedule_circuit(c, ctx->n, K, dbl ? 3 : 4, S);

@@ -1,0 +1,120 @@
+// Types shared by host code, the precompiled kernels and the kernels
+// generated at run time (NVRTC): kept free of standard-library headers.
+#pragma once
+
+#if defined(__CUDACC_RTC__)
+typedef unsigned long long uint64_t;
+typedef long long int64_t;
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned char uint8_t;
+typedef decltype(sizeof(0)) size_t;
+#else
+#include <cstdint>
+#endif
+
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+#define SD_HD __host__ __device__
+#else
+#define SD_HD
+#endif
+
+namespace sd {
+
+constexpr int kRegBits = 4;   // amplitudes per thread = 16
+constexpr int kLaneBits = 5;
+
+// OK_C1 parameters: had = 1: S^b H S^a (apply S^a, then H, then S^b);
+// had = 0: X^x S^a (apply S^a, then X if x).  H is the unnormalised
+// butterfly; its 1/sqrt(2) is part of the pass's deferred scale.
+inline SD_HD int32_t c1_pack(int had, int a, int b, int x) { return had | (a << 1) | (b << 3) | (x << 5); }
+inline SD_HD int c1_had(int32_t v) { return v & 1; }
+inline SD_HD int c1_a(int32_t v) { return (v >> 1) & 3; }
+inline SD_HD int c1_b(int32_t v) { return (v >> 3) & 3; }
+inline SD_HD int c1_x(int32_t v) { return (v >> 5) & 1; }
+
+// Device ops of a round: one-qubit Cliffords on register slot `slot` with
+// the OK_C1 parameters in `arg` (D_HAD: S^b H S^a, D_MONO: X^x S^a), or
+// diagonal ops with table index `arg`.  pad = 1 on the D_DIAG op that also
+// applies the pass's scale.
+enum DevOpKind : int32_t { D_HAD = 0, D_MONO = 1, D_PHASE = 3, D_DIAG = 4 };
+
+struct DevOp {
+    int32_t kind, slot, arg, pad;
+};
+constexpr int kMaxPassOps = 1024;
+
+struct DevRound {
+    uint8_t reg_pos[4];
+    uint8_t lane_pos[5];  // lane bit i <-> tile position lane_pos[i]
+    uint8_t warp_pos[7];
+    int32_t op_begin, op_end;
+    int32_t perm;       // -1 or index of an in-tile permutation applied on the round's smem write
+    int32_t flags;      // 1: load from global, 2: store to global
+    int32_t term_begin; // group-exponential terms staged in shared memory for this round
+    int32_t term_count;
+};
+
+struct DevPass {
+    int32_t round_begin, n_rounds;
+    int32_t n_outer;
+    int32_t scale_in_diag;   // 1 if the deferred scale is folded into a D_DIAG op
+    int32_t max_stage;       // most terms staged by one round
+    int32_t pad;
+    double scale;            // 2^(-h/2) for h Hadamards in the pass
+    uint8_t tile_bits[16];
+    uint8_t outer_bits[48];
+};
+
+// In-tile linear permutation (a run of CNOTs whose targets are tile qubits):
+// the amplitude at tile index l of the tile with outer bits h moves to
+// (xor of col[p] over set bits p of l) ^ (xor of ocol[k] over set outer bits k).
+struct DevPerm {
+    uint32_t col[16];
+    uint32_t ocol[48];
+};
+
+// Per-round diagonal descriptor: terms sorted by their register projection
+// (class s = the bits of the mask on the round's 4 register positions).
+// Class s occupies [off[s], off[s+1]) of the round's staged terms.
+struct DevDiag {
+    int32_t off[17];
+    int32_t pad;
+};
+
+// Per-round phase descriptor (S/CZ layer).
+struct DevPhase {
+    uint64_t sp, sm;      // global masks
+    int64_t adj_base;     // index of n adjacency masks (symmetric) in the mask pool
+    int64_t up_base;      // index of n upper adjacency masks
+    int32_t lin_s[4];     // +1 / -1 / 0: S or S^dag on the qubit of register slot i
+    int32_t quad;         // bit (i*4+j) set: CZ between register slots i<j
+    int32_t n;
+};
+
+
+// Term of a group exponential staged in shared memory for one tile: its
+// Q0.64 angle with the sign of the tile's outer bits folded in, and its mask
+// on the fixed (lane and warp) tile positions of the round.
+struct StagedTerm {
+    uint64_t q;
+    uint32_t ml;
+    uint32_t pad;
+};
+
+// Pointers a tile-pass kernel reads besides the state.
+struct KParams {
+    const DevPass *passes;
+    const DevRound *rounds;
+    const DevOp *ops;
+    const DevPerm *perms;
+    const DevDiag *diags;
+    const DevPhase *phases;
+    const uint64_t *term_mo;
+    const uint32_t *term_ml;
+    const int64_t *term_q;
+    const uint64_t *mask_pool;
+    int c;
+};
+
+}  // namespace sd

@@ -1,0 +1,474 @@
+// Run-time specialisation of tile passes.
+//
+// The interpreter kernel (kernels.cu) reads each pass's rounds and ops from
+// device memory and dispatches on them; for large states that dispatch and
+// the register traffic it forces dominate a pass.  Here every pass of a
+// schedule becomes straight-line CUDA C++ -- layouts, register slots,
+// Clifford phases, class boundaries, global offsets and scales as
+// constants -- compiled once with NVRTC for sm_103a and launched through the
+// driver API.  The generated kernels compute what the interpreter computes,
+// op for op, with the same device helpers (tile_device.cuh).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "jit.h"
+#include "jit_headers.inc"   // kJitDevTypes, kJitTileDevice: the two device headers as text
+
+namespace sd {
+namespace {
+
+struct Nvrtc {
+    bool ok = false;
+    nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *,
+                          const char *const *) = nullptr;
+    nvrtcResult (*compile)(nvrtcProgram, int, const char *const *) = nullptr;
+    nvrtcResult (*log_size)(nvrtcProgram, size_t *) = nullptr;
+    nvrtcResult (*log)(nvrtcProgram, char *) = nullptr;
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t *) = nullptr;
+    nvrtcResult (*cubin)(nvrtcProgram, char *) = nullptr;
+    nvrtcResult (*destroy)(nvrtcProgram *) = nullptr;
+    nvrtcResult (*version)(int *, int *) = nullptr;
+};
+
+struct Driver {
+    bool ok = false;
+    CUresult (*load)(CUmodule *, const void *) = nullptr;
+    CUresult (*get_function)(CUfunction *, CUmodule, const char *) = nullptr;
+    CUresult (*set_attr)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                       unsigned, CUstream, void **, void **) = nullptr;
+    CUresult (*occupancy)(int *, CUfunction, int, size_t) = nullptr;
+};
+
+std::mutex g_mu;
+Nvrtc g_nvrtc;
+Driver g_drv;
+bool g_init = false;
+std::string g_why;
+std::map<std::string, CUmodule> g_modules;   // source hash -> loaded module
+
+template <typename F>
+bool sym(void *h, const char *name, F &f) {
+    f = reinterpret_cast<F>(dlsym(h, name));
+    return f != nullptr;
+}
+
+template <typename F>
+bool drv_sym(const char *name, F &f) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+        cudaGetLastError();
+        return false;
+    }
+    f = reinterpret_cast<F>(p);
+    return true;
+}
+
+void init_locked() {
+    if (g_init) return;
+    g_init = true;
+    const char *cands[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                           "/usr/local/cuda/lib64/libnvrtc.so"};
+    void *h = nullptr;
+    for (const char *c : cands)
+        if ((h = dlopen(c, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) {
+        g_why = "libnvrtc not found";
+        return;
+    }
+    g_nvrtc.ok = sym(h, "nvrtcCreateProgram", g_nvrtc.create) &&
+                 sym(h, "nvrtcCompileProgram", g_nvrtc.compile) &&
+                 sym(h, "nvrtcGetProgramLogSize", g_nvrtc.log_size) &&
+                 sym(h, "nvrtcGetProgramLog", g_nvrtc.log) &&
+                 sym(h, "nvrtcGetCUBINSize", g_nvrtc.cubin_size) &&
+                 sym(h, "nvrtcGetCUBIN", g_nvrtc.cubin) &&
+                 sym(h, "nvrtcDestroyProgram", g_nvrtc.destroy) &&
+                 sym(h, "nvrtcVersion", g_nvrtc.version);
+    if (!g_nvrtc.ok) {
+        g_why = "libnvrtc lacks a needed symbol";
+        return;
+    }
+    g_drv.ok = drv_sym("cuModuleLoadData", g_drv.load) &&
+               drv_sym("cuModuleGetFunction", g_drv.get_function) &&
+               drv_sym("cuFuncSetAttribute", g_drv.set_attr) &&
+               drv_sym("cuLaunchKernel", g_drv.launch) &&
+               drv_sym("cuOccupancyMaxActiveBlocksPerMultiprocessor", g_drv.occupancy);
+    if (!g_drv.ok) g_why = "CUDA driver entry points unavailable";
+}
+
+// ------------------------------------------------------------ code generation
+
+std::string hex64(uint64_t v) {
+    char b[40];
+    snprintf(b, sizeof b, "0x%llxull", (unsigned long long)v);
+    return b;
+}
+std::string hex32(uint32_t v) {
+    char b[24];
+    snprintf(b, sizeof b, "0x%xu", v);
+    return b;
+}
+std::string dbl(double v) {
+    char b[48];
+    snprintf(b, sizeof b, "%.17g", v);
+    return b;
+}
+
+// XOR of col(p) over the tile positions p that the thread's lane and warp
+// bits select in round R (32-bit or 64-bit result).
+std::string thread_expr(const DevRound &R, int K, const std::function<uint64_t(int)> &col, bool wide) {
+    std::ostringstream o;
+    o << (wide ? "(0ull" : "(0u");
+    for (int i = 0; i < kLaneBits; i++) {
+        uint64_t v = col(R.lane_pos[i]);
+        if (v) o << " ^ ((" << (wide ? "uint64_t" : "uint32_t") << ")((lane >> " << i << ") & 1) * "
+                 << (wide ? hex64(v) : hex32((uint32_t)v)) << ")";
+    }
+    for (int i = 0; i < K - 9; i++) {
+        uint64_t v = col(R.warp_pos[i]);
+        if (v) o << " ^ ((" << (wide ? "uint64_t" : "uint32_t") << ")((warp >> " << i << ") & 1) * "
+                 << (wide ? hex64(v) : hex32((uint32_t)v)) << ")";
+    }
+    o << ")";
+    return o.str();
+}
+
+std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
+    const DevPass &P = S.passes[pi];
+    const int K = S.K, c = S.c;
+    const int NT = 1 << (K - 4);
+    const int E = dbl_state ? 1 : 2;
+    const int NCOPY = (1 << K) / E / NT;
+    auto gbit = [&](int p) -> uint64_t { return (uint64_t)1 << P.tile_bits[p]; };
+    auto swc = [&](int p) -> uint64_t { return swizzle_col(p, c); };
+    auto lcol = [&](int p) -> uint64_t { return (uint64_t)1 << p; };
+    const double pass_scale = P.scale_in_diag ? 1.0 : P.scale;
+    std::ostringstream o;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") sdp_" << pi
+      << "(A *__restrict__ psi, sd::KParams kp) {\n"
+      << "  using namespace sd;\n"
+      << "  constexpr int K = " << K << ", NT = " << NT << ", E = " << E << ";\n"
+      << "  extern __shared__ __align__(16) unsigned char smraw[];\n"
+      << "  A *X = reinterpret_cast<A *>(smraw);\n"
+      << "  A *Pf = X + (1 << K);\n"
+      << "  StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf + (1 << K));\n"
+      << "  (void)ST;\n"
+      << "  __shared__ A TW[256];\n"
+      << "  __shared__ uint64_t OUTT[4][256];\n"
+      << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n"
+      << "  (void)lane; (void)warp;\n"
+      << "  for (int i = tid; i < 256; i += NT) {\n"
+      << "    double sn, cs;\n    sincospi((double)i / 128.0, &sn, &cs);\n"
+      << "    TW[i].x = (T)cs;\n    TW[i].y = (T)sn;\n";
+    for (int byte = 0; byte < 4; byte++) {
+        o << "    OUTT[" << byte << "][i] = 0ull";
+        for (int b = 0; b < 8; b++) {
+            const int k = byte * 8 + b;
+            if (k < P.n_outer)
+                o << " | ((uint64_t)((i >> " << b << ") & 1) << " << (int)P.outer_bits[k] << ")";
+        }
+        o << ";\n";
+    }
+    o << "  }\n  __syncthreads();\n";
+    // copy l = (tid + k NT) E: bit j of l is bit (j - log2 E) of tid for the low K-4 such bits
+    const int le = E == 2 ? 1 : 0;
+    o << "  const uint64_t sp_tid = 0ull";
+    for (int j = le; j < K; j++)
+        if (j - le < K - 4) o << " | ((uint64_t)((tid >> " << (j - le) << ") & 1) << " << (int)P.tile_bits[j] << ")";
+    o << ";\n  const long long ntiles = " << (1LL << (n - K)) << "ll;\n"
+      << "  auto deposit = [&](long long t) -> uint64_t {\n"
+      << "    return OUTT[0][t & 255] | OUTT[1][(t >> 8) & 255] | OUTT[2][(t >> 16) & 255] | OUTT[3][(t >> 24) & 255];\n"
+      << "  };\n"
+      << "  auto prefetch = [&](long long t) {\n    const uint64_t xo = deposit(t) | sp_tid;\n";
+    for (int k = 0; k < NCOPY; k++) {
+        const uint64_t lk = (uint64_t)k * NT * E;
+        uint64_t off = 0;
+        for (int j = 0; j < K; j++)
+            if ((lk >> j) & 1) off |= gbit(j);
+        o << "    cp_async16(Pf + (tid * E + " << lk << "), psi + (xo | " << hex64(off) << "));\n";
+    }
+    o << "    cp_async_commit();\n  };\n";
+    // swizzle of an arbitrary tile index (perm rounds)
+    o << "  auto swz = [](uint32_t v) -> uint32_t {\n    return 0u";
+    for (int p = 0; p < K; p++) o << " ^ (((v >> " << p << ") & 1u) * " << hex32((uint32_t)swc(p)) << ")";
+    o << ";\n  };\n  (void)swz;\n";
+    o << "  long long tile = blockIdx.x;\n  if (tile < ntiles) prefetch(tile);\n"
+      << "  for (; tile < ntiles; tile += gridDim.x) {\n"
+      << "    const uint64_t xo = deposit(tile);\n"
+      << "    A a[16];\n";
+    for (int r = 0; r < P.n_rounds; r++) {
+        const DevRound &R = S.rounds[P.round_begin + r];
+        o << "    { // round " << r << "\n";
+        if (r == 0) o << "      cp_async_wait_all();\n";
+        o << "      __syncthreads();\n";
+        if (R.term_count > 0) {
+            o << "      for (int j = tid; j < " << R.term_count << "; j += NT) {\n"
+              << "        const int g = " << R.term_begin << " + j;\n"
+              << "        const uint64_t q = (uint64_t)__ldg(kp.term_q + g);\n"
+              << "        StagedTerm t;\n"
+              << "        t.q = (__popcll(xo & __ldg(kp.term_mo + g)) & 1) ? (0ull - q) : q;\n"
+              << "        t.ml = __ldg(kp.term_ml + g);\n        t.pad = 0;\n        ST[j] = t;\n"
+              << "      }\n      __syncthreads();\n";
+        }
+        o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
+          << "      const uint32_t sw = " << thread_expr(R, K, swc, false) << ";\n"
+          << "      (void)lf; (void)sw;\n";
+        if (r == 0) {
+            for (int s = 0; s < 16; s++) {
+                uint32_t l = 0;
+                for (int i = 0; i < 4; i++)
+                    if ((s >> i) & 1) l |= 1u << R.reg_pos[i];
+                o << "      a[" << s << "] = Pf[lf | " << hex32(l) << "];\n";
+            }
+            o << "      __syncthreads();\n"
+              << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);\n";
+        } else {
+            for (int s = 0; s < 16; s++) {
+                uint32_t cs = 0;
+                for (int i = 0; i < 4; i++)
+                    if ((s >> i) & 1) cs ^= (uint32_t)swc(R.reg_pos[i]);
+                o << "      a[" << s << "] = X[sw ^ " << hex32(cs) << "];\n";
+            }
+        }
+        bool need_xf = (R.flags & 2) != 0;
+        for (int oi = R.op_begin; oi < R.op_end; oi++)
+            need_xf |= S.ops[oi].kind == D_PHASE;
+        if (need_xf) o << "      const uint64_t xf = xo | " << thread_expr(R, K, gbit, true) << ";\n";
+        for (int oi = R.op_begin; oi < R.op_end; oi++) {
+            const DevOp &op = S.ops[oi];
+            if (op.kind == D_HAD) {
+                o << "      had_fixed<" << op.slot << ", " << c1_a(op.arg) << ", " << c1_b(op.arg) << ">(a);\n";
+            } else if (op.kind == D_MONO) {
+                o << "      mono_fixed<" << op.slot << ", " << c1_a(op.arg) << ", " << c1_x(op.arg) << ">(a);\n";
+            } else if (op.kind == D_PHASE) {
+                o << "      { const int gq[4] = {" << (int)P.tile_bits[R.reg_pos[0]] << ", "
+                  << (int)P.tile_bits[R.reg_pos[1]] << ", " << (int)P.tile_bits[R.reg_pos[2]] << ", "
+                  << (int)P.tile_bits[R.reg_pos[3]] << "};\n"
+                  << "        phase_apply(a, xf, gq, kp.phases[" << op.arg << "], kp.mask_pool); }\n";
+            } else {
+                const DevDiag &d = S.diags[op.arg];
+                const double sc = op.pad ? P.scale : 1.0;
+                o << "      { uint64_t G[16];\n";
+                for (int s = 0; s < 16; s++) {
+                    const int b = d.off[s], e = d.off[s + 1];
+                    if (b == e) {
+                        o << "        G[" << s << "] = 0ull;\n";
+                        continue;
+                    }
+                    o << "        { uint64_t acc0 = 0ull, acc1 = 0ull;\n"
+                      << "          #pragma unroll 4\n"
+                      << "          for (int j = " << b << "; j + 1 < " << e << "; j += 2) {\n"
+                      << "            const StagedTerm t0 = ST[j], t1 = ST[j + 1];\n"
+                      << "            acc0 += (__popc(lf & t0.ml) & 1) ? (0ull - t0.q) : t0.q;\n"
+                      << "            acc1 += (__popc(lf & t1.ml) & 1) ? (0ull - t1.q) : t1.q;\n"
+                      << "          }\n";
+                    if ((e - b) & 1)
+                        o << "          { const StagedTerm t0 = ST[" << e - 1 << "];\n"
+                          << "            acc0 += (__popc(lf & t0.ml) & 1) ? (0ull - t0.q) : t0.q; }\n";
+                    o << "          G[" << s << "] = acc0 + acc1; }\n";
+                }
+                o << "        wht16(G);\n"
+                  << "        #pragma unroll\n"
+                  << "        for (int s = 0; s < 16; s++) a[s] = rotate_tw(a[s], G[s], TW, (T)" << dbl(sc) << ");\n"
+                  << "      }\n";
+            }
+        }
+        if (R.flags & 2) {
+            for (int s = 0; s < 16; s++) {
+                uint64_t g = 0;
+                for (int i = 0; i < 4; i++)
+                    if ((s >> i) & 1) g |= gbit(R.reg_pos[i]);
+                if (pass_scale != 1.0)
+                    o << "      { A w = a[" << s << "]; w.x *= (T)" << dbl(pass_scale) << "; w.y *= (T)"
+                      << dbl(pass_scale) << "; psi[xf | " << hex64(g) << "] = w; }\n";
+                else
+                    o << "      psi[xf | " << hex64(g) << "] = a[" << s << "];\n";
+            }
+        } else if (R.perm >= 0) {
+            if (r > 0) o << "      __syncthreads();\n";
+            o << "      { const DevPerm &pm = kp.perms[" << R.perm << "];\n"
+              << "        uint32_t l = 0u;\n"
+              << "        #pragma unroll\n"
+              << "        for (int p = 0; p < K; p++) if ((lf >> p) & 1) l ^= pm.col[p];\n"
+              << "        for (int k = 0; k < " << P.n_outer << "; k++) if ((tile >> k) & 1) l ^= pm.ocol[k];\n"
+              << "        const uint32_t base = swz(l);\n"
+              << "        const uint32_t c0 = swz(pm.col[" << (int)R.reg_pos[0] << "]), c1 = swz(pm.col["
+              << (int)R.reg_pos[1] << "]), c2 = swz(pm.col[" << (int)R.reg_pos[2] << "]), c3 = swz(pm.col["
+              << (int)R.reg_pos[3] << "]);\n"
+              << "        #pragma unroll\n"
+              << "        for (int s = 0; s < 16; s++) X[base ^ ((s & 1) ? c0 : 0u) ^ ((s & 2) ? c1 : 0u) ^ "
+                 "((s & 4) ? c2 : 0u) ^ ((s & 8) ? c3 : 0u)] = a[s];\n"
+              << "      }\n";
+        } else {
+            for (int s = 0; s < 16; s++) {
+                uint32_t cs = 0;
+                for (int i = 0; i < 4; i++)
+                    if ((s >> i) & 1) cs ^= (uint32_t)swc(R.reg_pos[i]);
+                o << "      X[sw ^ " << hex32(cs) << "] = a[" << s << "];\n";
+            }
+        }
+        o << "    }\n";
+    }
+    o << "  }\n}\n\n";
+    return o.str();
+}
+
+std::string cache_dir() {
+    const char *e = getenv("SD_JIT_CACHE");
+    if (e && *e) return e;
+    const char *x = getenv("XDG_CACHE_HOME");
+    if (x && *x) return std::string(x) + "/sd_jit";
+    const char *h = getenv("HOME");
+    return std::string(h && *h ? h : "/tmp") + "/.cache/sd_jit";
+}
+
+void mkdirs(const std::string &p) {
+    std::string cur;
+    std::stringstream ss(p);
+    std::string part;
+    if (!p.empty() && p[0] == '/') cur = "/";
+    while (std::getline(ss, part, '/')) {
+        if (part.empty()) continue;
+        cur += part + "/";
+        mkdir(cur.c_str(), 0755);
+    }
+}
+
+std::string compile_cubin(const std::string &src, std::string &cubin) {
+    nvrtcProgram prog;
+    const char *hdrs[] = {kJitDevTypes, kJitTileDevice};
+    const char *names[] = {"dev_types.h", "tile_device.cuh"};
+    if (g_nvrtc.create(&prog, src.c_str(), "sd_passes.cu", 2, hdrs, names) != NVRTC_SUCCESS)
+        return "nvrtcCreateProgram failed";
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG"};
+    nvrtcResult rc = g_nvrtc.compile(prog, 4, opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        g_nvrtc.log_size(prog, &ls);
+        std::string log(ls, '\0');
+        if (ls) g_nvrtc.log(prog, &log[0]);
+        g_nvrtc.destroy(&prog);
+        return "NVRTC compile failed: " + log.substr(0, 2000);
+    }
+    size_t cs = 0;
+    g_nvrtc.cubin_size(prog, &cs);
+    cubin.assign(cs, '\0');
+    g_nvrtc.cubin(prog, &cubin[0]);
+    g_nvrtc.destroy(&prog);
+    return "";
+}
+
+}  // namespace
+
+bool jit_available(std::string *why) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    init_locked();
+    if (why) *why = g_why;
+    return g_nvrtc.ok && g_drv.ok;
+}
+
+std::string jit_source(const Schedule &S, int n, bool dbl_state) {
+    std::ostringstream src;
+    src << "#include \"dev_types.h\"\n#include \"tile_device.cuh\"\n"
+        << "typedef " << (dbl_state ? "double" : "float") << " T;\n"
+        << "typedef " << (dbl_state ? "double2" : "float2") << " A;\n\n";
+    for (int p = 0; p < (int)S.passes.size(); p++) src << gen_pass(S, p, n, dbl_state);
+    return src.str();
+}
+
+std::string jit_compile_check(const std::string &src) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    init_locked();
+    if (!g_nvrtc.ok) return g_why;
+    std::string cubin;
+    return compile_cubin(src, cubin);
+}
+
+std::string jit_build(const Schedule &S, int n, bool dbl_state, JitProgram &out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    init_locked();
+    if (!(g_nvrtc.ok && g_drv.ok)) return g_why;
+    const std::string code = jit_source(S, n, dbl_state);
+    int maj = 0, min = 0;
+    g_nvrtc.version(&maj, &min);
+    const std::string key = std::to_string(std::hash<std::string>{}(code)) + "_" +
+                            std::to_string(code.size()) + "_nvrtc" + std::to_string(maj) + "." +
+                            std::to_string(min);
+    CUmodule mod = nullptr;
+    auto it = g_modules.find(key);
+    if (it != g_modules.end()) {
+        mod = it->second;
+    } else {
+        std::string cubin;
+        const std::string dir = cache_dir(), path = dir + "/" + key + ".cubin";
+        {
+            std::ifstream f(path, std::ios::binary);
+            if (f) cubin.assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+        }
+        if (cubin.empty()) {
+            std::string err = compile_cubin(code, cubin);
+            if (!err.empty()) return err;
+            mkdirs(dir);
+            const std::string tmp = path + ".tmp" + std::to_string(getpid());
+            std::ofstream f(tmp, std::ios::binary);
+            if (f) {
+                f.write(cubin.data(), (std::streamsize)cubin.size());
+                f.close();
+                rename(tmp.c_str(), path.c_str());
+            }
+        }
+        if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS) return "cuModuleLoadData failed";
+        g_modules[key] = mod;
+    }
+    out = JitProgram{};
+    out.module = mod;
+    out.K = S.K;
+    for (int p = 0; p < (int)S.passes.size(); p++) {
+        CUfunction f = nullptr;
+        const std::string name = "sdp_" + std::to_string(p);
+        if (g_drv.get_function(&f, mod, name.c_str()) != CUDA_SUCCESS) return "missing kernel " + name;
+        const size_t amp = dbl_state ? 16 : 8;
+        const size_t smem = 2 * (amp << S.K) + sizeof(StagedTerm) *
+                                                   (size_t)(S.passes[p].max_stage > 0 ? S.passes[p].max_stage : 1);
+        if (g_drv.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
+            return "cuFuncSetAttribute failed";
+        int occ = 0;
+        if (g_drv.occupancy(&occ, f, 1 << (S.K - 4), smem) != CUDA_SUCCESS) return "occupancy query failed";
+        out.funcs.push_back((void *)f);
+        out.occupancy.push_back(occ > 0 ? occ : 1);
+        out.smem.push_back(smem);
+    }
+    return "";
+}
+
+cudaError_t jit_launch(const JitProgram &jp, int pass, void *psi, const KParams &kp, int n, int num_sms,
+                       cudaStream_t st) {
+    const int64_t ntiles = (int64_t)1 << (n - jp.K);
+    int64_t grid = (int64_t)num_sms * jp.occupancy[pass];
+    if (grid > ntiles) grid = ntiles;
+    void *ps = psi;
+    KParams k = kp;
+    void *args[] = {&ps, &k};
+    CUresult r = g_drv.launch((CUfunction)jp.funcs[pass], (unsigned)grid, 1, 1, 1u << (jp.K - 4), 1, 1,
+                              (unsigned)jp.smem[pass], (CUstream)st, args, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+}  // namespace sd

@@ -16,289 +16,323 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "tile_device.cuh"
 
 namespace sd {
 namespace {
 
-template <typename T> struct VT;
-template <> struct VT<float> { using A = float2; };
-template <> struct VT<double> { using A = double2; };
+constexpr int kMaxRounds = 12;
 
-__device__ __forceinline__ int popc64(uint64_t v) { return __popcll(v); }
-
-// (cos 2 pi t, sin 2 pi t) of Q0.64 turns t, in the state precision.
-__device__ __forceinline__ void turns_sc(uint64_t t, float &s, float &c) {
-    int32_t hi = (int32_t)((t + 0x80000000ull) >> 32);   // nearest 2^-32 turn
-    float tf = (float)hi * 2.3283064365386963e-10f;
-    sincospif(2.0f * tf, &s, &c);
-}
-__device__ __forceinline__ void turns_sc(uint64_t t, double &s, double &c) {
-    double tf = (double)(int64_t)t * 5.421010862427522170e-20;   // 2^-64
-    sincospi(2.0 * tf, &s, &c);
+// Packed op word: kind (3 bits) | slot (2) | p1 (2) | p2 (2) | arg (23).
+// D_HAD: p1 = a, p2 = b; D_MONO: p1 = a, p2 = x; D_DIAG: p1 = scale flag.
+__host__ __device__ __forceinline__ int32_t pack_op(const DevOp &o) {
+    int p1 = 0, p2 = 0, arg = 0;
+    if (o.kind == D_HAD) { p1 = c1_a(o.arg); p2 = c1_b(o.arg); }
+    else if (o.kind == D_MONO) { p1 = c1_a(o.arg); p2 = c1_x(o.arg); }
+    else { p1 = o.pad; arg = o.arg; }
+    return o.kind | (o.slot << 3) | (p1 << 5) | (p2 << 7) | (arg << 9);
 }
 
-// a <- a * i^k
-template <typename A>
-__device__ __forceinline__ A mul_ipow(A a, int k) {
-    A r = a;
-    switch (k & 3) {
-    case 1: r.x = -a.y; r.y = a.x; break;
-    case 2: r.x = -a.x; r.y = -a.y; break;
-    case 3: r.x = a.y; r.y = -a.x; break;
-    default: break;
-    }
-    return r;
-}
-
-// a <- a * exp(-2 pi i t) * sc
-template <typename T, typename A>
-__device__ __forceinline__ A rotate(A a, uint64_t t, T sc) {
-    T s, c;
-    turns_sc(t, s, c);
-    c *= sc;
-    s *= sc;
-    A r;
-    r.x = a.x * c + a.y * s;
-    r.y = a.y * c - a.x * s;
-    return r;
-}
-
-template <int I, typename A>
-__device__ __forceinline__ void h_fixed(A *a) {
-#pragma unroll
-    for (int s = 0; s < 16; s++)
-        if (!((s >> I) & 1)) {
-            A u = a[s], v = a[s | (1 << I)];
-            a[s].x = u.x + v.x;
-            a[s].y = u.y + v.y;
-            a[s | (1 << I)].x = u.x - v.x;
-            a[s | (1 << I)].y = u.y - v.y;
-        }
-}
-
-template <int I, typename A>
-__device__ __forceinline__ void s_fixed(A *a, int k) {
-#pragma unroll
-    for (int s = 0; s < 16; s++)
-        if ((s >> I) & 1) a[s] = mul_ipow(a[s], k);
-}
-
-template <typename A>
-__device__ __forceinline__ void h_slot(A *a, int slot) {
-    switch (slot) {
-    case 0: h_fixed<0>(a); break;
-    case 1: h_fixed<1>(a); break;
-    case 2: h_fixed<2>(a); break;
-    default: h_fixed<3>(a); break;
-    }
-}
-
-template <typename A>
-__device__ __forceinline__ void s_slot(A *a, int slot, int k) {
-    switch (slot) {
-    case 0: s_fixed<0>(a, k); break;
-    case 1: s_fixed<1>(a, k); break;
-    case 2: s_fixed<2>(a, k); break;
-    default: s_fixed<3>(a, k); break;
-    }
-}
-
-// In-place Walsh-Hadamard transform of 16 register values.
-__device__ __forceinline__ void wht16(uint64_t *G) {
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int s = 0; s < 16; s++)
-            if (!((s >> i) & 1)) {
-                uint64_t u = G[s], v = G[s | (1 << i)];
-                G[s] = u + v;
-                G[s | (1 << i)] = u - v;
-            }
-}
-__device__ __forceinline__ void wht16(double *G) {
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int s = 0; s < 16; s++)
-            if (!((s >> i) & 1)) {
-                double u = G[s], v = G[s | (1 << i)];
-                G[s] = u + v;
-                G[s | (1 << i)] = u - v;
-            }
-}
-
-// Group exponential on the thread's 16 amplitudes: T(s) = sum_j q_j
-// (-1)^{|x & m_j|} with x = xf | (register bits of s).  Terms arrive sorted
-// by their register projection u (class u); per class the sum over the
-// fixed bits gives G[u], and a 4-level WHT over the register bits gives T.
-template <typename T, typename A>
-__device__ __forceinline__ void diag_apply(A *a, uint64_t xf, const DevDiag &d,
-                                           const uint64_t *__restrict__ tm,
-                                           const int64_t *__restrict__ tq, T sc) {
-    uint64_t G[16];
-#pragma unroll
-    for (int s = 0; s < 16; s++) {
-        uint64_t acc = 0;
-        const int64_t b = d.base;
-        for (int j = d.off[s]; j < d.off[s + 1]; j++) {
-            uint64_t m = __ldg(tm + b + j);
-            uint64_t q = (uint64_t)__ldg(tq + b + j);
-            acc += (popc64(xf & m) & 1) ? (0 - q) : q;
-        }
-        G[s] = acc;
-    }
-    wht16(G);
-#pragma unroll
-    for (int s = 0; s < 16; s++) a[s] = rotate<T>(a[s], G[s], sc);
-}
-
-// S/CZ layer: a(x) *= i^{k(x)}, k = |x&sp| - |x&sm| + 2 sum_CZ x_c x_t.
-template <typename A>
-__device__ __forceinline__ void phase_apply(A *a, uint64_t xf, const int *gq, const DevPhase &ph,
-                                            const uint64_t *__restrict__ pool) {
-    int kb = popc64(xf & ph.sp) - popc64(xf & ph.sm);
-    int Q = 0;
-    uint64_t rest = xf;
-    while (rest) {
-        int c = __ffsll((long long)rest) - 1;
-        rest &= rest - 1;
-        Q ^= popc64(xf & __ldg(pool + ph.up_base + c)) & 1;
-    }
-    kb += 2 * Q;
-    int lin[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-        lin[i] = ph.lin_s[i] + 2 * (popc64(xf & __ldg(pool + ph.adj_base + gq[i])) & 1);
-#pragma unroll
-    for (int s = 0; s < 16; s++) {
-        int k = kb;
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-            if ((s >> i) & 1) k += lin[i];
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int j = i + 1; j < 4; j++)
-                if (((s >> i) & 1) && ((s >> j) & 1) && ((ph.quad >> (i * 4 + j)) & 1)) k += 2;
-        a[s] = mul_ipow(a[s], k);
-    }
-}
-
-struct KParams {
-    const DevPass *passes;
-    const DevRound *rounds;
-    const DevOp *ops;
-    const DevPerm *perms;
-    const DevDiag *diags;
-    const DevPhase *phases;
-    const uint64_t *term_masks;
-    const int64_t *term_q;
-    const uint64_t *mask_pool;
-    int c;
-};
-
+// One pass over the state vector.  Per tile: the prefetch buffer (filled by
+// cp.async while the previous tile was processed) is read in the load
+// layout; the next tile's prefetch is issued; the rounds run on registers
+// with exchanges through the swizzled buffer; the last round stores.
+// Per-round thread layouts (tile index, swizzled index, global offset of the
+// fixed bits) come from tables built once per block.
 template <typename T, int K>
 __global__ void __launch_bounds__(1 << (K - 4))
 tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KParams kp) {
     using A = typename VT<T>::A;
+    constexpr int NT = 1 << (K - 4);
+    constexpr int NW = NT / 32;
+    constexpr int E = 16 / (int)sizeof(A);            // amplitudes per 16-byte copy
+    constexpr int NCOPY = (1 << K) / E / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
-    A *sm = reinterpret_cast<A *>(smraw);
+    A *X = reinterpret_cast<A *>(smraw);                // exchange buffer (swizzled)
+    A *Pf = X + (1 << K);                               // prefetch buffer (tile order)
+    StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf + (1 << K));
     __shared__ DevPass P;
-    __shared__ DevRound RR[12];
+    __shared__ DevRound RR[kMaxRounds];
     __shared__ uint32_t swzc[16];
+    __shared__ A TW[256];
+    __shared__ uint64_t SPLO[256], SPHI[32];           // spread of tile index bits 0-7, 8-12
+    __shared__ uint64_t OUTT[4][256];                  // deposit of tile number bytes
+    __shared__ uint32_t LTL[kMaxRounds][32], LTW[kMaxRounds][NW];   // lf | swz(lf) << 16
+    __shared__ uint64_t XL[kMaxRounds][32], XW[kMaxRounds][NW];     // spread(lf) parts
+    __shared__ uint32_t RCS[kMaxRounds][4];            // register column | swizzled << 16
+    __shared__ uint64_t RG[kMaxRounds][4];             // global offset of register slot
+    __shared__ int32_t OPS[kMaxPassOps];
     const int tid = threadIdx.x;
     if (tid == 0) P = kp.passes[pass_idx];
     __syncthreads();
-    if (tid < P.n_rounds) RR[tid] = kp.rounds[P.round_begin + tid];
+    const int nr = P.n_rounds;
+    if (tid < nr) RR[tid] = kp.rounds[P.round_begin + tid];
     if (tid < K) {
         uint32_t col = 1u << tid;
         if (tid >= kp.c) {
-            uint32_t span = (1u << kp.c) - 1u;
+            const uint32_t span = (1u << kp.c) - 1u;
             col |= 1u + (uint32_t)((tid - kp.c) % (int)span);
         }
         swzc[tid] = col;
     }
+    for (int i = tid; i < 256; i += NT) {
+        double sn, cs;
+        sincospi((double)i / 128.0, &sn, &cs);
+        TW[i].x = (T)cs;
+        TW[i].y = (T)sn;
+        uint64_t v = 0;
+        for (int b = 0; b < 8 && b < K; b++)
+            if ((i >> b) & 1) v |= (uint64_t)1 << P.tile_bits[b];
+        SPLO[i] = v;
+        if (i < 32) {
+            uint64_t w = 0;
+            for (int b = 0; b < 5 && 8 + b < K; b++)
+                if ((i >> b) & 1) w |= (uint64_t)1 << P.tile_bits[8 + b];
+            SPHI[i] = w;
+        }
+#pragma unroll
+        for (int byte = 0; byte < 4; byte++) {
+            uint64_t o = 0;
+            for (int b = 0; b < 8; b++) {
+                const int k = byte * 8 + b;
+                if (k < P.n_outer && ((i >> b) & 1)) o |= (uint64_t)1 << P.outer_bits[k];
+            }
+            OUTT[byte][i] = o;
+        }
+    }
+    __syncthreads();
+    {
+        const int op0 = RR[0].op_begin, nops = RR[nr - 1].op_end - op0;
+        for (int i = tid; i < nops; i += NT) OPS[i] = pack_op(kp.ops[op0 + i]);
+        for (int i = tid; i < nr * (32 + NW); i += NT) {
+            const int r = i / (32 + NW), k = i % (32 + NW);
+            const DevRound &R = RR[r];
+            uint32_t lfp = 0;
+            if (k < 32) {
+                for (int b = 0; b < 5; b++)
+                    if ((k >> b) & 1) lfp |= 1u << R.lane_pos[b];
+            } else {
+                for (int b = 0; b < K - 9; b++)
+                    if (((k - 32) >> b) & 1) lfp |= 1u << R.warp_pos[b];
+            }
+            uint32_t sw = 0;
+            for (int p = 0; p < K; p++)
+                if ((lfp >> p) & 1) sw ^= swzc[p];
+            const uint64_t xp = SPLO[lfp & 255] | SPHI[lfp >> 8];
+            if (k < 32) {
+                LTL[r][k] = lfp | (sw << 16);
+                XL[r][k] = xp;
+            } else {
+                LTW[r][k - 32] = lfp | (sw << 16);
+                XW[r][k - 32] = xp;
+            }
+        }
+        for (int i = tid; i < nr * 4; i += NT) {
+            const int r = i >> 2, s = i & 3, p = RR[r].reg_pos[s];
+            RCS[r][s] = (1u << p) | (swzc[p] << 16);
+            RG[r][s] = (uint64_t)1 << P.tile_bits[p];
+        }
+    }
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5;
     const int64_t ntiles = (int64_t)1 << (n - K);
-    const int nr = P.n_rounds;
+    const int op0 = RR[0].op_begin;
     const T pass_scale = P.scale_in_diag ? (T)1 : (T)P.scale;
     const T diag_scale = (T)P.scale;
+    auto deposit = [&](int64_t t) -> uint64_t {
+        return OUTT[0][t & 255] | OUTT[1][(t >> 8) & 255] | OUTT[2][(t >> 16) & 255] |
+               OUTT[3][(t >> 24) & 255];
+    };
+    auto prefetch = [&](int64_t t) {
+        const uint64_t xo = deposit(t);
+#pragma unroll
+        for (int k = 0; k < NCOPY; k++) {
+            const uint32_t l = (uint32_t)(tid + k * NT) * E;
+            cp_async16(Pf + l, psi + (xo | SPLO[l & 255] | SPHI[l >> 8]));
+        }
+        cp_async_commit();
+    };
 
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        uint64_t xo = 0;
-        for (int k = 0; k < P.n_outer; k++)
-            xo |= (uint64_t)((tile >> k) & 1) << P.outer_bits[k];
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) prefetch(tile);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const uint64_t xo = deposit(tile);
         A a[16];
         for (int r = 0; r < nr; r++) {
             const DevRound &R = RR[r];
-            uint32_t lf = 0;
-#pragma unroll
-            for (int i = 0; i < 5; i++) lf |= (uint32_t)((lane >> i) & 1) << R.lane_pos[i];
-#pragma unroll
-            for (int i = 0; i < K - 9; i++) lf |= (uint32_t)((warp >> i) & 1) << R.warp_pos[i];
-            uint64_t xf = xo;
-            uint32_t sw = 0;
-#pragma unroll
-            for (int p = 0; p < K; p++)
-                if ((lf >> p) & 1) {
-                    xf |= (uint64_t)1 << P.tile_bits[p];
-                    sw ^= swzc[p];
+            if (r == 0) cp_async_wait_all();
+            __syncthreads();
+            if (R.term_count > 0) {
+                for (int j = tid; j < R.term_count; j += NT) {
+                    const int g = R.term_begin + j;
+                    const uint64_t q = (uint64_t)__ldg(kp.term_q + g);
+                    StagedTerm t;
+                    t.q = (__popcll(xo & __ldg(kp.term_mo + g)) & 1) ? (0 - q) : q;
+                    t.ml = __ldg(kp.term_ml + g);
+                    t.pad = 0;
+                    ST[j] = t;
                 }
-            int gq[4];
+                __syncthreads();
+            }
+            const uint32_t v = LTL[r][lane] ^ LTW[r][warp];
+            const uint32_t lf = v & 0xffffu, sw = v >> 16;
+            uint32_t lreg[4], cs[4];
 #pragma unroll
-            for (int i = 0; i < 4; i++) gq[i] = P.tile_bits[R.reg_pos[i]];
+            for (int i = 0; i < 4; i++) {
+                const uint32_t c2 = RCS[r][i];
+                lreg[i] = c2 & 0xffffu;
+                cs[i] = c2 >> 16;
+            }
             if (r == 0) {
 #pragma unroll
                 for (int s = 0; s < 16; s++) {
-                    uint64_t x = xf;
+                    uint32_t l = lf;
 #pragma unroll
                     for (int i = 0; i < 4; i++)
-                        if ((s >> i) & 1) x |= (uint64_t)1 << gq[i];
-                    a[s] = psi[x];
+                        if ((s >> i) & 1) l |= lreg[i];
+                    a[s] = Pf[l];
                 }
+                __syncthreads();
+                if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
             } else {
-                uint32_t cs[4];
-#pragma unroll
-                for (int i = 0; i < 4; i++) cs[i] = swzc[R.reg_pos[i]];
 #pragma unroll
                 for (int s = 0; s < 16; s++) {
                     uint32_t ad = sw;
 #pragma unroll
                     for (int i = 0; i < 4; i++)
                         if ((s >> i) & 1) ad ^= cs[i];
-                    a[s] = sm[ad];
+                    a[s] = X[ad];
                 }
             }
+            const uint64_t xf = xo | XL[r][lane] | XW[r][warp];
             for (int o = R.op_begin; o < R.op_end; o++) {
-                const DevOp op = kp.ops[o];
-                switch (op.kind) {
-                case D_H: h_slot(a, op.slot); break;
-                case D_S: s_slot(a, op.slot, 1); break;
-                case D_SDG: s_slot(a, op.slot, 3); break;
-                case D_PHASE: phase_apply(a, xf, gq, kp.phases[op.arg], kp.mask_pool); break;
+                const int32_t code = OPS[o - op0];
+                switch (code & 511) {
+                case D_HAD | (0 << 3) | (0 << 5) | (0 << 7): had_fixed<0, 0, 0>(a); break;
+                case D_HAD | (0 << 3) | (0 << 5) | (1 << 7): had_fixed<0, 0, 1>(a); break;
+                case D_HAD | (0 << 3) | (0 << 5) | (2 << 7): had_fixed<0, 0, 2>(a); break;
+                case D_HAD | (0 << 3) | (0 << 5) | (3 << 7): had_fixed<0, 0, 3>(a); break;
+                case D_HAD | (0 << 3) | (1 << 5) | (0 << 7): had_fixed<0, 1, 0>(a); break;
+                case D_HAD | (0 << 3) | (1 << 5) | (1 << 7): had_fixed<0, 1, 1>(a); break;
+                case D_HAD | (0 << 3) | (1 << 5) | (2 << 7): had_fixed<0, 1, 2>(a); break;
+                case D_HAD | (0 << 3) | (1 << 5) | (3 << 7): had_fixed<0, 1, 3>(a); break;
+                case D_HAD | (0 << 3) | (2 << 5) | (0 << 7): had_fixed<0, 2, 0>(a); break;
+                case D_HAD | (0 << 3) | (2 << 5) | (1 << 7): had_fixed<0, 2, 1>(a); break;
+                case D_HAD | (0 << 3) | (2 << 5) | (2 << 7): had_fixed<0, 2, 2>(a); break;
+                case D_HAD | (0 << 3) | (2 << 5) | (3 << 7): had_fixed<0, 2, 3>(a); break;
+                case D_HAD | (0 << 3) | (3 << 5) | (0 << 7): had_fixed<0, 3, 0>(a); break;
+                case D_HAD | (0 << 3) | (3 << 5) | (1 << 7): had_fixed<0, 3, 1>(a); break;
+                case D_HAD | (0 << 3) | (3 << 5) | (2 << 7): had_fixed<0, 3, 2>(a); break;
+                case D_HAD | (0 << 3) | (3 << 5) | (3 << 7): had_fixed<0, 3, 3>(a); break;
+                case D_HAD | (1 << 3) | (0 << 5) | (0 << 7): had_fixed<1, 0, 0>(a); break;
+                case D_HAD | (1 << 3) | (0 << 5) | (1 << 7): had_fixed<1, 0, 1>(a); break;
+                case D_HAD | (1 << 3) | (0 << 5) | (2 << 7): had_fixed<1, 0, 2>(a); break;
+                case D_HAD | (1 << 3) | (0 << 5) | (3 << 7): had_fixed<1, 0, 3>(a); break;
+                case D_HAD | (1 << 3) | (1 << 5) | (0 << 7): had_fixed<1, 1, 0>(a); break;
+                case D_HAD | (1 << 3) | (1 << 5) | (1 << 7): had_fixed<1, 1, 1>(a); break;
+                case D_HAD | (1 << 3) | (1 << 5) | (2 << 7): had_fixed<1, 1, 2>(a); break;
+                case D_HAD | (1 << 3) | (1 << 5) | (3 << 7): had_fixed<1, 1, 3>(a); break;
+                case D_HAD | (1 << 3) | (2 << 5) | (0 << 7): had_fixed<1, 2, 0>(a); break;
+                case D_HAD | (1 << 3) | (2 << 5) | (1 << 7): had_fixed<1, 2, 1>(a); break;
+                case D_HAD | (1 << 3) | (2 << 5) | (2 << 7): had_fixed<1, 2, 2>(a); break;
+                case D_HAD | (1 << 3) | (2 << 5) | (3 << 7): had_fixed<1, 2, 3>(a); break;
+                case D_HAD | (1 << 3) | (3 << 5) | (0 << 7): had_fixed<1, 3, 0>(a); break;
+                case D_HAD | (1 << 3) | (3 << 5) | (1 << 7): had_fixed<1, 3, 1>(a); break;
+                case D_HAD | (1 << 3) | (3 << 5) | (2 << 7): had_fixed<1, 3, 2>(a); break;
+                case D_HAD | (1 << 3) | (3 << 5) | (3 << 7): had_fixed<1, 3, 3>(a); break;
+                case D_HAD | (2 << 3) | (0 << 5) | (0 << 7): had_fixed<2, 0, 0>(a); break;
+                case D_HAD | (2 << 3) | (0 << 5) | (1 << 7): had_fixed<2, 0, 1>(a); break;
+                case D_HAD | (2 << 3) | (0 << 5) | (2 << 7): had_fixed<2, 0, 2>(a); break;
+                case D_HAD | (2 << 3) | (0 << 5) | (3 << 7): had_fixed<2, 0, 3>(a); break;
+                case D_HAD | (2 << 3) | (1 << 5) | (0 << 7): had_fixed<2, 1, 0>(a); break;
+                case D_HAD | (2 << 3) | (1 << 5) | (1 << 7): had_fixed<2, 1, 1>(a); break;
+                case D_HAD | (2 << 3) | (1 << 5) | (2 << 7): had_fixed<2, 1, 2>(a); break;
+                case D_HAD | (2 << 3) | (1 << 5) | (3 << 7): had_fixed<2, 1, 3>(a); break;
+                case D_HAD | (2 << 3) | (2 << 5) | (0 << 7): had_fixed<2, 2, 0>(a); break;
+                case D_HAD | (2 << 3) | (2 << 5) | (1 << 7): had_fixed<2, 2, 1>(a); break;
+                case D_HAD | (2 << 3) | (2 << 5) | (2 << 7): had_fixed<2, 2, 2>(a); break;
+                case D_HAD | (2 << 3) | (2 << 5) | (3 << 7): had_fixed<2, 2, 3>(a); break;
+                case D_HAD | (2 << 3) | (3 << 5) | (0 << 7): had_fixed<2, 3, 0>(a); break;
+                case D_HAD | (2 << 3) | (3 << 5) | (1 << 7): had_fixed<2, 3, 1>(a); break;
+                case D_HAD | (2 << 3) | (3 << 5) | (2 << 7): had_fixed<2, 3, 2>(a); break;
+                case D_HAD | (2 << 3) | (3 << 5) | (3 << 7): had_fixed<2, 3, 3>(a); break;
+                case D_HAD | (3 << 3) | (0 << 5) | (0 << 7): had_fixed<3, 0, 0>(a); break;
+                case D_HAD | (3 << 3) | (0 << 5) | (1 << 7): had_fixed<3, 0, 1>(a); break;
+                case D_HAD | (3 << 3) | (0 << 5) | (2 << 7): had_fixed<3, 0, 2>(a); break;
+                case D_HAD | (3 << 3) | (0 << 5) | (3 << 7): had_fixed<3, 0, 3>(a); break;
+                case D_HAD | (3 << 3) | (1 << 5) | (0 << 7): had_fixed<3, 1, 0>(a); break;
+                case D_HAD | (3 << 3) | (1 << 5) | (1 << 7): had_fixed<3, 1, 1>(a); break;
+                case D_HAD | (3 << 3) | (1 << 5) | (2 << 7): had_fixed<3, 1, 2>(a); break;
+                case D_HAD | (3 << 3) | (1 << 5) | (3 << 7): had_fixed<3, 1, 3>(a); break;
+                case D_HAD | (3 << 3) | (2 << 5) | (0 << 7): had_fixed<3, 2, 0>(a); break;
+                case D_HAD | (3 << 3) | (2 << 5) | (1 << 7): had_fixed<3, 2, 1>(a); break;
+                case D_HAD | (3 << 3) | (2 << 5) | (2 << 7): had_fixed<3, 2, 2>(a); break;
+                case D_HAD | (3 << 3) | (2 << 5) | (3 << 7): had_fixed<3, 2, 3>(a); break;
+                case D_HAD | (3 << 3) | (3 << 5) | (0 << 7): had_fixed<3, 3, 0>(a); break;
+                case D_HAD | (3 << 3) | (3 << 5) | (1 << 7): had_fixed<3, 3, 1>(a); break;
+                case D_HAD | (3 << 3) | (3 << 5) | (2 << 7): had_fixed<3, 3, 2>(a); break;
+                case D_HAD | (3 << 3) | (3 << 5) | (3 << 7): had_fixed<3, 3, 3>(a); break;
+                case D_MONO | (0 << 3) | (0 << 5) | (1 << 7): mono_fixed<0, 0, 1>(a); break;
+                case D_MONO | (0 << 3) | (1 << 5) | (0 << 7): mono_fixed<0, 1, 0>(a); break;
+                case D_MONO | (0 << 3) | (1 << 5) | (1 << 7): mono_fixed<0, 1, 1>(a); break;
+                case D_MONO | (0 << 3) | (2 << 5) | (0 << 7): mono_fixed<0, 2, 0>(a); break;
+                case D_MONO | (0 << 3) | (2 << 5) | (1 << 7): mono_fixed<0, 2, 1>(a); break;
+                case D_MONO | (0 << 3) | (3 << 5) | (0 << 7): mono_fixed<0, 3, 0>(a); break;
+                case D_MONO | (0 << 3) | (3 << 5) | (1 << 7): mono_fixed<0, 3, 1>(a); break;
+                case D_MONO | (1 << 3) | (0 << 5) | (1 << 7): mono_fixed<1, 0, 1>(a); break;
+                case D_MONO | (1 << 3) | (1 << 5) | (0 << 7): mono_fixed<1, 1, 0>(a); break;
+                case D_MONO | (1 << 3) | (1 << 5) | (1 << 7): mono_fixed<1, 1, 1>(a); break;
+                case D_MONO | (1 << 3) | (2 << 5) | (0 << 7): mono_fixed<1, 2, 0>(a); break;
+                case D_MONO | (1 << 3) | (2 << 5) | (1 << 7): mono_fixed<1, 2, 1>(a); break;
+                case D_MONO | (1 << 3) | (3 << 5) | (0 << 7): mono_fixed<1, 3, 0>(a); break;
+                case D_MONO | (1 << 3) | (3 << 5) | (1 << 7): mono_fixed<1, 3, 1>(a); break;
+                case D_MONO | (2 << 3) | (0 << 5) | (1 << 7): mono_fixed<2, 0, 1>(a); break;
+                case D_MONO | (2 << 3) | (1 << 5) | (0 << 7): mono_fixed<2, 1, 0>(a); break;
+                case D_MONO | (2 << 3) | (1 << 5) | (1 << 7): mono_fixed<2, 1, 1>(a); break;
+                case D_MONO | (2 << 3) | (2 << 5) | (0 << 7): mono_fixed<2, 2, 0>(a); break;
+                case D_MONO | (2 << 3) | (2 << 5) | (1 << 7): mono_fixed<2, 2, 1>(a); break;
+                case D_MONO | (2 << 3) | (3 << 5) | (0 << 7): mono_fixed<2, 3, 0>(a); break;
+                case D_MONO | (2 << 3) | (3 << 5) | (1 << 7): mono_fixed<2, 3, 1>(a); break;
+                case D_MONO | (3 << 3) | (0 << 5) | (1 << 7): mono_fixed<3, 0, 1>(a); break;
+                case D_MONO | (3 << 3) | (1 << 5) | (0 << 7): mono_fixed<3, 1, 0>(a); break;
+                case D_MONO | (3 << 3) | (1 << 5) | (1 << 7): mono_fixed<3, 1, 1>(a); break;
+                case D_MONO | (3 << 3) | (2 << 5) | (0 << 7): mono_fixed<3, 2, 0>(a); break;
+                case D_MONO | (3 << 3) | (2 << 5) | (1 << 7): mono_fixed<3, 2, 1>(a); break;
+                case D_MONO | (3 << 3) | (3 << 5) | (0 << 7): mono_fixed<3, 3, 0>(a); break;
+                case D_MONO | (3 << 3) | (3 << 5) | (1 << 7): mono_fixed<3, 3, 1>(a); break;
+                case D_PHASE: {
+                    int gq[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++) gq[i] = P.tile_bits[R.reg_pos[i]];
+                    phase_apply(a, xf, gq, kp.phases[code >> 9], kp.mask_pool);
+                    break;
+                }
                 default:
-                    diag_apply<T>(a, xf, kp.diags[op.arg], kp.term_masks, kp.term_q,
-                                  op.pad ? diag_scale : (T)1);
+                    if ((code & 7) == D_DIAG)
+                        diag_apply(a, lf, kp.diags[code >> 9], ST, TW,
+                                   ((code >> 5) & 1) ? diag_scale : (T)1);
                     break;
                 }
             }
             if (R.flags & 2) {
+                uint64_t goff[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) goff[i] = RG[r][i];
 #pragma unroll
                 for (int s = 0; s < 16; s++) {
                     uint64_t x = xf;
 #pragma unroll
                     for (int i = 0; i < 4; i++)
-                        if ((s >> i) & 1) x |= (uint64_t)1 << gq[i];
-                    A v = a[s];
-                    v.x *= pass_scale;
-                    v.y *= pass_scale;
-                    psi[x] = v;
+                        if ((s >> i) & 1) x |= goff[i];
+                    A w = a[s];
+                    w.x *= pass_scale;
+                    w.y *= pass_scale;
+                    psi[x] = w;
                 }
             } else {
-                __syncthreads();
-                uint32_t base, cs[4];
+                uint32_t base = sw;
                 if (R.perm >= 0) {
+                    if (r > 0) __syncthreads();   // others may still read what this thread overwrites
                     const DevPerm &pm = kp.perms[R.perm];
                     uint32_t l = 0;
 #pragma unroll
@@ -312,16 +346,13 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
                         if ((l >> p) & 1) base ^= swzc[p];
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
-                        uint32_t v = pm.col[R.reg_pos[i]], w = 0;
+                        const uint32_t cv = pm.col[R.reg_pos[i]];
+                        uint32_t w = 0;
 #pragma unroll
                         for (int p = 0; p < K; p++)
-                            if ((v >> p) & 1) w ^= swzc[p];
+                            if ((cv >> p) & 1) w ^= swzc[p];
                         cs[i] = w;
                     }
-                } else {
-                    base = sw;
-#pragma unroll
-                    for (int i = 0; i < 4; i++) cs[i] = swzc[R.reg_pos[i]];
                 }
 #pragma unroll
                 for (int s = 0; s < 16; s++) {
@@ -329,9 +360,8 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
 #pragma unroll
                     for (int i = 0; i < 4; i++)
                         if ((s >> i) & 1) ad ^= cs[i];
-                    sm[ad] = a[s];
+                    X[ad] = a[s];
                 }
-                __syncthreads();
             }
         }
     }
@@ -347,22 +377,24 @@ template <typename T, int K>
 cudaError_t run_tile(void *psi, int n, const DevSchedule &S, int pass, int num_sms, cudaStream_t st) {
     using A = typename VT<T>::A;
     const int threads = 1 << (K - 4);
-    const size_t smem = sizeof(A) << K;
     const int d = sizeof(T) == 8;
+    const size_t smem = tile_smem_bytes<A, K>(S.host_passes[pass].max_stage);
+    const size_t smem_max = tile_smem_limit();
+    if (smem > smem_max) return cudaErrorInvalidConfiguration;
     if (!g_occ.init[d][K]) {
         cudaError_t e = cudaFuncSetAttribute(tile_pass_kernel<T, K>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return e;
-        int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tile_pass_kernel<T, K>, threads, smem);
-        if (e != cudaSuccess) return e;
-        g_occ.blocks[d][K] = b > 0 ? b : 1;
         g_occ.init[d][K] = true;
     }
+    int b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tile_pass_kernel<T, K>, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (b < 1) b = 1;
     KParams kp{S.passes, S.rounds, S.ops, S.perms, S.diags, S.phases,
-               S.term_masks, S.term_q, S.mask_pool, S.c};
+               S.term_mo, S.term_ml, S.term_q, S.mask_pool, S.c};
     int64_t ntiles = (int64_t)1 << (n - K);
-    int64_t grid = (int64_t)num_sms * g_occ.blocks[d][K];
+    int64_t grid = (int64_t)num_sms * b;
     if (grid > ntiles) grid = ntiles;
     tile_pass_kernel<T, K><<<(unsigned)grid, threads, smem, st>>>(reinterpret_cast<A *>(psi), n, pass, kp);
     return cudaGetLastError();
@@ -408,8 +440,31 @@ onchip_kernel(typename VT<T>::A *__restrict__ psi, int n, KFlat kf, int64_t reps
     for (int64_t rep = 0; rep < reps; rep++) {
         for (int64_t o = 0; o < kf.n_ops; o++) {
             const DevFlatOp op = kf.ops[o];
-            if (op.kind == OK_H || op.kind == OK_S || op.kind == OK_SDG) {
+            if (op.kind == OK_C1) {
                 const int64_t bq = (int64_t)1 << op.q;
+                const int had = c1_had(op.q2), pa = c1_a(op.q2), pb = c1_b(op.q2), xx = c1_x(op.q2);
+                for (int64_t i = tid; i < N / 2; i += nt) {
+                    int64_t lo = i & (bq - 1);
+                    int64_t y = ((i - lo) << 1) | lo;
+                    A u = st[y], w = mul_ipow(st[y | bq], pa);
+                    if (had) {
+                        A o0, o1;
+                        o0.x = (u.x + w.x) * r2;
+                        o0.y = (u.y + w.y) * r2;
+                        o1.x = (u.x - w.x) * r2;
+                        o1.y = (u.y - w.y) * r2;
+                        st[y] = o0;
+                        st[y | bq] = mul_ipow(o1, pb);
+                    } else if (xx) {
+                        st[y] = w;
+                        st[y | bq] = u;
+                    } else {
+                        st[y | bq] = w;
+                    }
+                }
+            } else if (is_1q(op.kind)) {
+                const int64_t bq = (int64_t)1 << op.q;
+                const int k = op.kind == OK_S ? 1 : (op.kind == OK_Z ? 2 : 3);
                 for (int64_t i = tid; i < N / 2; i += nt) {
                     int64_t lo = i & (bq - 1);
                     int64_t y = ((i - lo) << 1) | lo;
@@ -419,8 +474,12 @@ onchip_kernel(typename VT<T>::A *__restrict__ psi, int n, KFlat kf, int64_t reps
                         st[y].y = (u.y + v.y) * r2;
                         st[y | bq].x = (u.x - v.x) * r2;
                         st[y | bq].y = (u.y - v.y) * r2;
+                    } else if (op.kind == OK_X) {
+                        A u = st[y];
+                        st[y] = st[y | bq];
+                        st[y | bq] = u;
                     } else {
-                        st[y | bq] = mul_ipow(st[y | bq], op.kind == OK_S ? 1 : 3);
+                        st[y | bq] = mul_ipow(st[y | bq], k);
                     }
                 }
             } else if (op.kind == OK_CNOT) {
@@ -672,6 +731,12 @@ grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restr
 
 
 }  // namespace
+
+size_t tile_pass_smem(bool dbl, int K, int max_stage) {
+    const size_t amp = dbl ? 16 : 8;
+    return 2 * (amp << K) + 16 * (size_t)(max_stage > 0 ? max_stage : 1);
+}
+size_t tile_pass_smem_limit() { return tile_smem_limit(); }
 
 cudaError_t launch_tile_pass(bool dbl, void *psi, int n, const DevSchedule &S, int pass, int num_sms,
                              cudaStream_t st) {

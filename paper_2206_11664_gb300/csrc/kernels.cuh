@@ -18,7 +18,8 @@ struct DevSchedule {
     DevPerm *perms = nullptr;
     DevDiag *diags = nullptr;
     DevPhase *phases = nullptr;
-    uint64_t *term_masks = nullptr;
+    uint64_t *term_mo = nullptr;
+    uint32_t *term_ml = nullptr;
     int64_t *term_q = nullptr;
     uint64_t *mask_pool = nullptr;
     std::vector<DevPass> host_passes;  // for launch-side decisions
@@ -40,6 +41,10 @@ struct DevCircuit {
     uint64_t *phase_sp = nullptr, *phase_sm = nullptr;   // per phase layer
     uint64_t *phase_up = nullptr;                         // n per phase layer
 };
+
+// Dynamic shared memory of a tile pass and its limit.
+size_t tile_pass_smem(bool dbl, int K, int max_stage);
+size_t tile_pass_smem_limit();
 
 cudaError_t launch_tile_pass(bool dbl, void *psi, int n, const DevSchedule &S, int pass,
                              int num_sms, cudaStream_t st);

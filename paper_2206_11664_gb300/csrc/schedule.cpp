@@ -15,6 +15,7 @@
 // the registers are written back to shared memory between rounds.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <map>
 #include <set>
 
@@ -131,6 +132,128 @@ void append_group_step(const Plan &plan, int g, double f, double dt,
     append_clifford(plan, g, false, c);
 }
 
+// ------------------------------------------------------------ 1q canonical form
+
+namespace {
+
+using C2 = std::complex<double>;
+struct M2 {
+    C2 a, b, c, d;  // [[a, b], [c, d]]
+};
+M2 mul(const M2 &x, const M2 &y) {  // x * y
+    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c,
+            x.c * y.b + x.d * y.d};
+}
+M2 spow(int a);
+M2 gate_matrix(int32_t kind, int32_t par = 0);
+M2 c1_matrix(int32_t v) {
+    M2 m = spow(c1_a(v));
+    if (c1_had(v)) m = mul(spow(c1_b(v)), mul(gate_matrix(OK_H), m));
+    else if (c1_x(v)) m = mul(gate_matrix(OK_X), m);
+    return m;
+}
+M2 gate_matrix(int32_t kind, int32_t par) {
+    const double r = std::sqrt(0.5);
+    if (kind == OK_C1) return c1_matrix(par);
+    const C2 I(0, 1);
+    switch (kind) {
+    case OK_H: return {r, r, r, -r};
+    case OK_S: return {1.0, 0.0, 0.0, I};
+    case OK_SDG: return {1.0, 0.0, 0.0, -I};
+    case OK_Z: return {1.0, 0.0, 0.0, -1.0};
+    default: return {0.0, 1.0, 1.0, 0.0};  // OK_X
+    }
+}
+M2 spow(int a) {
+    const C2 p = std::pow(C2(0, 1), a);
+    return {1.0, 0.0, 0.0, p};
+}
+bool close(const M2 &x, const M2 &y, C2 ph) {
+    auto d = [&](C2 u, C2 v) { return std::abs(u - ph * v); };
+    return d(x.a, y.a) + d(x.b, y.b) + d(x.c, y.c) + d(x.d, y.d) < 1e-9;
+}
+void emit_c1(std::vector<FlatOp> &out, int q, int had, int a, int b, int x) {
+    if (!had && a == 0 && x == 0) return;   // identity
+    out.push_back(FlatOp{OK_C1, q, c1_pack(had, a, b, x), -1, uint64_t(1) << q});
+}
+// Canonical op (application order) and phase (eighth turns) of M.
+void canonical(const M2 &M, int q, std::vector<FlatOp> &out, int &phase8) {
+    const M2 H = gate_matrix(OK_H), X = gate_matrix(OK_X);
+    for (int k = 0; k < 8; k++) {
+        const C2 ph = std::polar(1.0, M_PI * k / 4.0);
+        for (int a = 0; a < 4; a++) {
+            if (close(M, spow(a), ph)) {
+                emit_c1(out, q, 0, a, 0, 0);
+                phase8 += k;
+                return;
+            }
+            if (close(M, mul(X, spow(a)), ph)) {
+                emit_c1(out, q, 0, a, 0, 1);
+                phase8 += k;
+                return;
+            }
+            for (int b = 0; b < 4; b++)
+                if (close(M, mul(spow(b), mul(H, spow(a))), ph)) {
+                    emit_c1(out, q, 1, a, b, 0);
+                    phase8 += k;
+                    return;
+                }
+        }
+    }
+}
+
+}  // namespace
+
+void canonicalize_1q(Circuit &c, int n) {
+    std::vector<std::vector<int>> run(n);   // pending op indices per qubit
+    std::vector<std::vector<FlatOp>> repl(c.ops.size());
+    std::vector<char> drop(c.ops.size(), 0);
+    int phase8 = 0;
+    auto flush = [&](int q) {
+        if (run[q].empty()) return;
+        M2 M = {1.0, 0.0, 0.0, 1.0};
+        for (int j : run[q]) M = mul(gate_matrix(c.ops[j].kind, c.ops[j].q2), M);
+        for (int j : run[q]) drop[j] = 1;
+        canonical(M, q, repl[run[q].front()], phase8);
+        run[q].clear();
+    };
+    for (size_t j = 0; j < c.ops.size(); j++) {
+        const FlatOp &op = c.ops[j];
+        if (is_1q(op.kind)) {
+            run[op.q].push_back((int)j);
+            continue;
+        }
+        uint64_t touched = op.kind == OK_CNOT ? ((uint64_t(1) << op.q) | (uint64_t(1) << op.q2))
+                                               : op.support;
+        for (int q = 0; q < n; q++)
+            if ((touched >> q) & 1) flush(q);
+    }
+    for (int q = 0; q < n; q++) flush(q);
+    std::vector<FlatOp> ops;
+    for (size_t j = 0; j < c.ops.size(); j++) {
+        for (auto &r : repl[j]) ops.push_back(r);
+        if (!drop[j]) ops.push_back(c.ops[j]);
+    }
+    c.ops.swap(ops);
+    phase8 &= 7;
+    if (phase8 == 0) return;
+    // e^{i pi k/4} = exp(-2 pi i (-k/8)): a constant term of -k/8 turn
+    const int64_t q0 = (int64_t)(uint64_t(8 - phase8) << 61);
+    for (auto &op : c.ops)
+        if (op.kind == OK_DIAG) {
+            c.diags[op.idx].masks.push_back(0);
+            c.diags[op.idx].q.push_back(q0);
+            return;
+        }
+    DiagLayer D;
+    D.group = -1;
+    D.frac = 0.0;
+    D.masks.push_back(0);
+    D.q.push_back(q0);
+    c.diags.push_back(D);
+    c.ops.push_back(FlatOp{OK_DIAG, -1, -1, (int32_t)c.diags.size() - 1, 0});
+}
+
 // ------------------------------------------------------------ scheduler
 
 namespace {
@@ -181,6 +304,9 @@ void assign_layout(DevRound &R, int K, int c, bool global_io) {
         for (int i = 0; i < 4; i++) isreg |= R.reg_pos[i] == p;
         if (!isreg) rest.push_back(p);
     }
+    // Lane bits 0..c-1 must span the c bank-selecting bits of the swizzled
+    // address (conflict-free shared accesses; coalesced global accesses in
+    // load/store rounds, where they are tile positions 0..c-1).
     std::vector<int> lanes;
     if (global_io) {
         for (int p = 0; p < c; p++) lanes.push_back(p);
@@ -189,7 +315,7 @@ void assign_layout(DevRound &R, int K, int c, bool global_io) {
     } else {
         std::vector<uint32_t> cols;
         for (int p : rest) {
-            if ((int)lanes.size() >= kLaneBits) break;
+            if ((int)lanes.size() >= c) break;
             std::vector<uint32_t> t = cols;
             t.push_back(swizzle_col(p, c));
             if (rank_cols(t, c) > rank_cols(cols, c)) {
@@ -202,12 +328,10 @@ void assign_layout(DevRound &R, int K, int c, bool global_io) {
                 std::find(lanes.begin(), lanes.end(), p) == lanes.end())
                 lanes.push_back(p);
     }
-    std::sort(lanes.begin(), lanes.end());
-    int li = 0, wi = 0;
-    for (int p : rest) {
-        if (std::find(lanes.begin(), lanes.end(), p) != lanes.end()) R.lane_pos[li++] = (uint8_t)p;
-        else R.warp_pos[wi++] = (uint8_t)p;
-    }
+    for (int i = 0; i < kLaneBits; i++) R.lane_pos[i] = (uint8_t)lanes[i];
+    int wi = 0;
+    for (int p : rest)
+        if (std::find(lanes.begin(), lanes.end(), p) == lanes.end()) R.warp_pos[wi++] = (uint8_t)p;
     for (; wi < 7; wi++) R.warp_pos[wi] = 0xff;
 }
 
@@ -264,7 +388,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             if (done[j] >= 0) continue;
             const FlatOp &op = circ.ops[j];
             int q = -1;
-            if (op.kind == OK_H || op.kind == OK_S || op.kind == OK_SDG) q = op.q;
+            if (is_1q(op.kind)) q = op.q;
             else if (op.kind == OK_CNOT) q = op.q2;
             if (q >= 0 && need[q] == INT32_MAX) need[q] = j;
         }
@@ -282,6 +406,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
 
         DevPass P{};
         P.round_begin = (int)S.rounds.size();
+        const int pass_op_begin = (int)S.ops.size();
         for (int p = 0; p < K; p++) P.tile_bits[p] = (uint8_t)tq[p];
         int no = 0;
         for (int q = 0; q < n; q++)
@@ -301,7 +426,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                 for (int j = first; j < N; j++) {
                     if (done[j] >= 0) continue;
                     const FlatOp &op = circ.ops[j];
-                    if ((op.kind == OK_H || op.kind == OK_S || op.kind == OK_SDG) && op.q == tq[p]) {
+                    if (is_1q(op.kind) && op.q == tq[p]) {
                         best = j;
                         break;
                     }
@@ -317,6 +442,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             R.perm = -1;
             R.flags = is_load ? 1 : 0;
             R.op_begin = (int)S.ops.size();
+            R.term_begin = (int)S.term_q.size();
             // -------- execute what is ready
             std::vector<Gate> perm_cnots;
             int executed = 0;
@@ -325,6 +451,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                 progress = false;
                 for (int j = first; j < N; j++) {
                     if (done[j] >= 0) continue;
+                    if ((int)S.ops.size() - pass_op_begin >= kMaxPassOps - 1) break;
                     const FlatOp &op = circ.ops[j];
                     bool ok = true;
                     for (int p : preds[j]) {
@@ -337,7 +464,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                     }
                     if (!ok) continue;
                     int slot = -1;
-                    if (op.kind == OK_H || op.kind == OK_S || op.kind == OK_SDG) {
+                    if (is_1q(op.kind)) {
                         int p = pos_of[op.q];
                         if (p < 0) continue;
                         for (int i = 0; i < 4; i++)
@@ -349,9 +476,18 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                             for (auto &g : perm_cnots) clash |= g.a == op.q || g.b == op.q;
                             if (clash) continue;
                         }
-                        DevOp d{op.kind == OK_H ? D_H : (op.kind == OK_S ? D_S : D_SDG), slot, 0, 0};
+                        int32_t par;
+                        switch (op.kind) {
+                        case OK_H: par = c1_pack(1, 0, 0, 0); break;
+                        case OK_S: par = c1_pack(0, 1, 0, 0); break;
+                        case OK_Z: par = c1_pack(0, 2, 0, 0); break;
+                        case OK_SDG: par = c1_pack(0, 3, 0, 0); break;
+                        case OK_X: par = c1_pack(0, 0, 0, 1); break;
+                        default: par = op.q2; break;
+                        }
+                        DevOp d{c1_had(par) ? D_HAD : D_MONO, slot, par, 0};
                         S.ops.push_back(d);
-                        if (op.kind == OK_H) h_count++;
+                        if (c1_had(par)) h_count++;
                     } else if (op.kind == OK_CNOT) {
                         if (pos_of[op.q2] < 0) continue;
                         perm_cnots.push_back(Gate{G_CNOT, op.q, op.q2});
@@ -403,12 +539,18 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                             cls[u].push_back((int)t);
                         }
                         DevDiag dd{};
-                        dd.base = (int64_t)S.term_q.size();
-                        int off = 0;
+                        int off = (int)S.term_q.size() - R.term_begin;
+                        uint64_t outer_mask = 0;
+                        for (int k = 0; k < no; k++) outer_mask |= uint64_t(1) << P.outer_bits[k];
                         for (int s = 0; s < 16; s++) {
                             dd.off[s] = off;
                             for (int t : cls[s]) {
-                                S.term_masks.push_back(D.masks[t] & ~regmask);
+                                uint32_t ml = 0;
+                                for (int p = 0; p < K; p++)
+                                    if (!((regmask >> tq[p]) & 1) && ((D.masks[t] >> tq[p]) & 1))
+                                        ml |= 1u << p;
+                                S.term_mo.push_back(D.masks[t] & outer_mask);
+                                S.term_ml.push_back(ml);
                                 S.term_q.push_back(D.q[t]);
                                 off++;
                             }
@@ -425,6 +567,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             }
             while (first < N && done[first] >= 0) first++;
             R.op_end = (int)S.ops.size();
+            R.term_count = (int)S.term_q.size() - R.term_begin;
             if (!perm_cnots.empty()) {
                 DevPerm pm{};
                 for (int p = 0; p < K; p++) {
@@ -461,6 +604,8 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             for (int i = 0; i < 4; i++) R.reg_pos[i] = (uint8_t)(c + i);
             R.perm = -1;
             R.op_begin = R.op_end = (int)S.ops.size();
+            R.term_begin = (int)S.term_q.size();
+            R.term_count = 0;
             R.flags = 0;
             S.rounds.push_back(R);
             nr++;
@@ -470,6 +615,9 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
         for (int r = P.round_begin; r < (int)S.rounds.size(); r++)
             assign_layout(S.rounds[r], K, c, (S.rounds[r].flags & 3) != 0);
         P.n_rounds = (int)S.rounds.size() - P.round_begin;
+        P.max_stage = 0;
+        for (int r = P.round_begin; r < (int)S.rounds.size(); r++)
+            P.max_stage = std::max(P.max_stage, S.rounds[r].term_count);
         P.scale = std::ldexp(1.0, -(h_count / 2)) * ((h_count & 1) ? std::sqrt(0.5) : 1.0);
         if (diag_op_index >= 0) {
             P.scale_in_diag = 1;

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include "dev_types.h"
+
 namespace sd {
 
 // ------------------------------------------------------------ planner
@@ -48,8 +50,18 @@ enum OpKind : int32_t {
     OK_SDG = 2,    // S^dag on qubit q
     OK_CNOT = 3,   // CNOT(c = q, t = q2)
     OK_PHASE = 4,  // diagonal quarter-turn layer: index into phase table
-    OK_DIAG = 5    // group exponential: index into diag table
+    OK_DIAG = 5,   // group exponential: index into diag table
+    OK_Z = 6,      // Pauli Z (= S S) on qubit q
+    OK_X = 7,      // Pauli X on qubit q
+    OK_C1 = 8      // canonical one-qubit Clifford on qubit q, parameters in q2 (c1_* below)
 };
+
+inline SD_HD bool is_1q(int32_t kind) {
+    return kind == OK_H || kind == OK_S || kind == OK_SDG || kind == OK_Z || kind == OK_X ||
+           kind == OK_C1;
+}
+
+
 
 struct FlatOp {
     int32_t kind;
@@ -90,59 +102,15 @@ void append_group_step(const Plan &plan, int g, double f, double dt,
 // Append only C_g (forward=true) or C_g^dag.
 void append_clifford(const Plan &plan, int g, bool forward, Circuit &c);
 
+// Merge every run of one-qubit gates on a qubit (no other op on that qubit
+// in between) into the canonical form S^a, X S^a or S^b H S^a of its
+// product (at most one Hadamard), and carry the dropped global phase
+// (a multiple of pi/4) exactly as a mask-0 term of the first group
+// exponential, or of an appended one if the circuit has none.
+void canonicalize_1q(Circuit &c, int n);
+
 // ------------------------------------------------------------ pass schedule
 
-constexpr int kRegBits = 4;   // amplitudes per thread = 16
-constexpr int kLaneBits = 5;
-
-enum DevOpKind : int32_t { D_H = 0, D_S = 1, D_SDG = 2, D_PHASE = 3, D_DIAG = 4 };
-
-struct DevOp {
-    int32_t kind, slot, arg, pad;
-};
-
-struct DevRound {
-    uint8_t reg_pos[4];
-    uint8_t lane_pos[5];
-    uint8_t warp_pos[7];
-    int32_t op_begin, op_end;
-    int32_t perm;       // -1 or index of an in-tile permutation applied on the round's smem write
-    int32_t flags;      // 1: load from global, 2: store to global
-};
-
-struct DevPass {
-    int32_t round_begin, n_rounds;
-    int32_t n_outer;
-    int32_t scale_in_diag;   // 1 if the deferred scale is folded into a D_DIAG op
-    double scale;            // 2^(-h/2) for h Hadamards in the pass
-    uint8_t tile_bits[16];
-    uint8_t outer_bits[48];
-};
-
-// In-tile linear permutation (a run of CNOTs whose targets are tile qubits):
-// the amplitude at tile index l of the tile with outer bits h moves to
-// (xor of col[p] over set bits p of l) ^ (xor of ocol[k] over set outer bits k).
-struct DevPerm {
-    uint32_t col[16];
-    uint32_t ocol[48];
-};
-
-// Per-round diagonal descriptor: terms sorted by their register projection.
-struct DevDiag {
-    int32_t off[17];      // class s occupies [off[s], off[s+1]) of the term arrays
-    int32_t pad;
-    int64_t base;         // first term in the term arrays
-};
-
-// Per-round phase descriptor (S/CZ layer).
-struct DevPhase {
-    uint64_t sp, sm;      // global masks
-    int64_t adj_base;     // index of n adjacency masks (symmetric) in the mask pool
-    int64_t up_base;      // index of n upper adjacency masks
-    int32_t lin_s[4];     // +1 / -1 / 0: S or S^dag on the qubit of register slot i
-    int32_t quad;         // bit (i*4+j) set: CZ between register slots i<j
-    int32_t n;
-};
 
 struct Schedule {
     int K = 0;
@@ -153,7 +121,8 @@ struct Schedule {
     std::vector<DevPerm> perms;
     std::vector<DevDiag> diags;
     std::vector<DevPhase> phases;
-    std::vector<uint64_t> term_masks;   // diag term pool: register-free mask part
+    std::vector<uint64_t> term_mo;      // diag term pool: mask on the outer qubits
+    std::vector<uint32_t> term_ml;      // diag term pool: mask on the round's fixed tile positions
     std::vector<int64_t> term_q;        // diag term pool: Q0.64 turns
     std::vector<uint64_t> mask_pool;    // phase adjacency pool
     int64_t diag_passes = 0;

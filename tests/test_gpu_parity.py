@@ -42,8 +42,8 @@ def _rand_state(rng, n):
     return v / np.linalg.norm(v)
 
 
-def _check(sd, h, psi0, dt_, steps, order, dtype, skip_rule=-1, tile_bits=0, pauli=False):
-    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(skip_rule=skip_rule, tile_bits=tile_bits)
+def _check(sd, h, psi0, dt_, steps, order, dtype, skip_rule=-1, tile_bits=0, pauli=False, jit=0):
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(skip_rule=skip_rule, tile_bits=tile_bits, jit=jit)
     groups = P.greedy_partition(h.x, h.z)
     ref = oracle.evolve(h, psi0, dt_, steps, order, groups)
     t = _dev(psi0, dtype)
@@ -225,3 +225,53 @@ def test_invalid_state_rejected(sd):
         sim.evolve(torch.zeros(1024, dtype=torch.complex64), 0.1, 1)
     with pytest.raises(sd.SDError):
         sim.evolve(torch.zeros(1024, dtype=torch.complex64, device="cuda"), 0.1, 1, order=3)
+
+
+# ---------------------------------------------------------------- run-time specialised passes
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_jit_heisenberg_and_random(sd, dtype):
+    """Passes compiled at run time (NVRTC) against the oracle: Hadamard-type
+    layers, CNOT permutations, S/CZ layers, several tiles, both orders."""
+    h = heisenberg_lattice(4, 4)
+    _check(sd, h, basis_state(16, neel_index(4, 4)), 0.02, 6, 1, dtype, jit=1)
+    rng = np.random.default_rng(61)
+    h2 = random_klocal(15, 50, rng, weights=(2, 3, 4))
+    _check(sd, h2, _rand_state(rng, 15), 0.05, 2, 2, dtype, skip_rule=0, jit=1)
+    _check(sd, h2, _rand_state(rng, 15), 0.05, 2, 1, dtype, tile_bits=11, jit=1)
+
+
+def test_jit_gradient(sd):
+    rng = np.random.default_rng(62)
+    n = 14
+    h = gradient_2local(n=n, m=20, rng=rng)
+    obs = z_average_observable(n)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(jit=1)
+    f, g = sim.grad(_dev(plus_state(n), "c128"), 0.05, 3, obs, 1)
+    f_ref, g_ref = oracle.grad(h, plus_state(n), 0.05, 3, 1, obs)
+    assert abs(f - f_ref) < 1e-12
+    assert np.max(np.abs(g - g_ref)) < 1e-9 * max(1.0, np.max(np.abs(g_ref)))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_full_size_heisenberg_n30(sd, dtype):
+    """The benchmark workload at full size (5x6 lattice, n = 30, Neel state,
+    dt = 0.02) in the benchmark's launch configuration: the grouped path must
+    agree with the independent per-Pauli kernel (itself checked against the
+    oracle above) and preserve the norm."""
+    import torch
+    h = heisenberg_lattice(5, 6)
+    cdt = torch.complex64 if dtype == "c64" else torch.complex128
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    steps = 2
+    a = torch.zeros(1 << 30, dtype=cdt, device="cuda")
+    a[neel_index(5, 6)] = 1
+    b = a.clone()
+    sim.evolve(a, 0.02, steps, 1)
+    sim.evolve_pauli(b, 0.02, steps, 1)
+    err = torch.linalg.vector_norm((a - b).to(torch.complex128)).item()
+    norm = torch.linalg.vector_norm(a.to(torch.complex128)).item()
+    assert err <= TOL[dtype], err
+    assert abs(norm - 1.0) < (1e-5 if dtype == "c64" else 1e-12)
+    del a, b
+    torch.cuda.empty_cache()
