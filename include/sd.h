@@ -182,6 +182,24 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
                           sd_dtype dtype, double dt, int64_t steps, int order,
                           void *cuda_stream);
 
+/* <psi|O|psi> like sd_expect, for callers that cannot allocate device
+ * memory (a fixed budget owned by another allocator, or a loop that must not
+ * pay cudaMalloc's implicit synchronisation).  The paper has no counterpart:
+ * this is a service of the library.  No context is needed and nothing is
+ * allocated: the scratch (per-block partial sums of one term, one result per
+ * term) lives in a file-scope static device array of about 41 KB that every
+ * GPU loading the library keeps until the process exits.  n qubits, state as
+ * in sd_evolve; mo <= 4096 terms (more gives SD_EINVAL, with a message in
+ * sd_last_error(NULL)); the observable arrays are host arrays; the value is
+ * written to *out_host after the stream is synchronised.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array, so calls that overlap on the GPU (other streams or
+ * host threads) race and must be serialised by the caller. */
+sd_status sd_expect_noalloc(int n, const void *d_state, sd_dtype dtype, int64_t mo,
+                            const uint64_t *ox, const uint64_t *oz, const double *oc,
+                            double *out_host, void *cuda_stream);
+
 /* Message for the last failing call on ctx (ctx may be NULL: last global error). */
 const char *sd_last_error(const sd_ctx *ctx);
 

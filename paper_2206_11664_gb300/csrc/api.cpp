@@ -506,6 +506,8 @@ sd_status get_grad_group(sd_ctx *ctx, int g, double f, double dt, GradGroup *&ou
 
 }  // namespace
 
+void sd::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 // =================================================================== C ABI
 
 extern "C" {

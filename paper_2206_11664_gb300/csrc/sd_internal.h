@@ -37,6 +37,9 @@ struct Plan {
     std::vector<GroupPlan> groups;
 };
 
+// Message returned by sd_last_error(NULL) on this thread.
+void set_last_error(const std::string &msg);
+
 // Returns an empty string on success, else the reason of failure.
 std::string make_plan(int n, int64_t m, const uint64_t *x, const uint64_t *z,
                       int skip_rule, Plan &out);
