@@ -198,6 +198,8 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
     CK(upload(P.allocs, D.term_ml, S.term_ml));
     CK(upload(P.allocs, D.term_q, S.term_q));
     CK(upload(P.allocs, D.mask_pool, S.mask_pool));
+    CK(upload(P.allocs, D.cst_mo, S.cst_mo));
+    CK(upload(P.allocs, D.cst_q, S.cst_q));
     P.passes = (int64_t)S.passes.size();
     P.rounds = (int64_t)S.rounds.size();
     P.diag_passes = S.diag_passes;
@@ -288,7 +290,7 @@ sd_status run_program(sd_ctx *ctx, bool dbl, Program &P, void *psi, int64_t reps
     if (P.jit.ok()) {
         const KParams kp{P.sched.passes, P.sched.rounds, P.sched.ops, P.sched.perms, P.sched.diags,
                          P.sched.phases, P.sched.term_mo, P.sched.term_ml, P.sched.term_q,
-                         P.sched.mask_pool, P.sched.c};
+                         P.sched.mask_pool, P.sched.cst_mo, P.sched.cst_q, P.sched.c};
         for (int64_t r = 0; r < reps; r++)
             for (int64_t p = 0; p < P.sched.n_passes; p++)
                 CK(jit_launch(P.jit, (int)p, psi, kp, ctx->n, ctx->num_sms, st));

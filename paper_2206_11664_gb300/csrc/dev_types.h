@@ -53,6 +53,11 @@ struct DevRound {
     int32_t flags;      // 1: load from global, 2: store to global
     int32_t term_begin; // group-exponential terms staged in shared memory for this round
     int32_t term_count;
+    // Terms whose masks meet no tile qubit of the round take one value on the
+    // whole tile: their signed sum is formed once per tile into slot c
+    // (pool range [cst_begin[c], cst_begin[c] + cst_count[c]) of cst_mo/cst_q).
+    int32_t cst_begin[4];
+    int32_t cst_count[4];
 };
 
 struct DevPass {
@@ -79,7 +84,7 @@ struct DevPerm {
 // Class s occupies [off[s], off[s+1]) of the round's staged terms.
 struct DevDiag {
     int32_t off[17];
-    int32_t pad;
+    int32_t cst;   // constant slot of the round holding this op's tile-constant terms, or -1
 };
 
 // Per-round phase descriptor (S/CZ layer).
@@ -114,6 +119,8 @@ struct KParams {
     const uint32_t *term_ml;
     const int64_t *term_q;
     const uint64_t *mask_pool;
+    const uint64_t *cst_mo;
+    const int64_t *cst_q;
     int c;
 };
 

@@ -160,6 +160,15 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     auto swc = [&](int p) -> uint64_t { return swizzle_col(p, c); };
     auto lcol = [&](int p) -> uint64_t { return (uint64_t)1 << p; };
     const double pass_scale = P.scale_in_diag ? 1.0 : P.scale;
+    // With a single group exponential in the pass, the pass scale goes into
+    // the rotation table instead of two multiplies per amplitude.
+    int n_diag = 0;
+    for (int r = 0; r < P.n_rounds; r++) {
+        const DevRound &R = S.rounds[P.round_begin + r];
+        for (int oi = R.op_begin; oi < R.op_end; oi++) n_diag += S.ops[oi].kind == D_DIAG;
+    }
+    const bool table_scaled = P.scale_in_diag && n_diag == 1;
+    const double table_scale = table_scaled ? P.scale : 1.0;
     std::ostringstream o;
     o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") sdp_" << pi
       << "(A *__restrict__ psi, sd::KParams kp) {\n"
@@ -172,11 +181,13 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
       << "  (void)ST;\n"
       << "  __shared__ A TW[256];\n"
       << "  __shared__ uint64_t OUTT[4][256];\n"
+      << "  __shared__ uint64_t CST[4];\n"
       << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n"
       << "  (void)lane; (void)warp;\n"
       << "  for (int i = tid; i < 256; i += NT) {\n"
       << "    double sn, cs;\n    sincospi((double)i / 128.0, &sn, &cs);\n"
-      << "    TW[i].x = (T)cs;\n    TW[i].y = (T)sn;\n";
+      << "    TW[i].x = (T)(cs * " << dbl(table_scale) << ");\n    TW[i].y = (T)(sn * " << dbl(table_scale)
+      << ");\n";
     for (int byte = 0; byte < 4; byte++) {
         o << "    OUTT[" << byte << "][i] = 0ull";
         for (int b = 0; b < 8; b++) {
@@ -218,14 +229,20 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         o << "    { // round " << r << "\n";
         if (r == 0) o << "      cp_async_wait_all();\n";
         o << "      __syncthreads();\n";
-        if (R.term_count > 0) {
+        const bool has_cst = (R.cst_count[0] | R.cst_count[1] | R.cst_count[2] | R.cst_count[3]) != 0;
+        if (R.term_count > 0 || has_cst) {
             o << "      for (int j = tid; j < " << R.term_count << "; j += NT) {\n"
               << "        const int g = " << R.term_begin << " + j;\n"
               << "        const uint64_t q = (uint64_t)__ldg(kp.term_q + g);\n"
               << "        StagedTerm t;\n"
               << "        t.q = (__popcll(xo & __ldg(kp.term_mo + g)) & 1) ? (0ull - q) : q;\n"
               << "        t.ml = __ldg(kp.term_ml + g);\n        t.pad = 0;\n        ST[j] = t;\n"
-              << "      }\n      __syncthreads();\n";
+              << "      }\n";
+            for (int cc = 0; cc < 4; cc++)
+                if (R.cst_count[cc] > 0)
+                    o << "      if (warp == " << (cc % (NT / 32)) << ") { const uint64_t v = warp_const_sum(xo, kp.cst_mo, kp.cst_q, "
+                      << R.cst_begin[cc] << ", " << R.cst_count[cc] << ", lane); if (lane == 0) CST[" << cc << "] = v; }\n";
+            o << "      __syncthreads();\n";
         }
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t sw = " << thread_expr(R, K, swc, false) << ";\n"
@@ -264,7 +281,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                   << "        phase_apply(a, xf, gq, kp.phases[" << op.arg << "], kp.mask_pool); }\n";
             } else {
                 const DevDiag &d = S.diags[op.arg];
-                const double sc = op.pad ? P.scale : 1.0;
+                const double sc = (op.pad && !table_scaled) ? P.scale : 1.0;
                 o << "      { uint64_t G[16];\n";
                 for (int s = 0; s < 16; s++) {
                     const int b = d.off[s], e = d.off[s + 1];
@@ -284,6 +301,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                           << "            acc0 += (__popc(lf & t0.ml) & 1) ? (0ull - t0.q) : t0.q; }\n";
                     o << "          G[" << s << "] = acc0 + acc1; }\n";
                 }
+                if (d.cst >= 0) o << "        G[0] += CST[" << d.cst << "];\n";
                 o << "        wht16(G);\n"
                   << "        #pragma unroll\n"
                   << "        for (int s = 0; s < 16; s++) a[s] = rotate_tw(a[s], G[s], TW, (T)" << dbl(sc) << ");\n"

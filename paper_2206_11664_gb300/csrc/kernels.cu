@@ -62,6 +62,7 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
     __shared__ uint32_t RCS[kMaxRounds][4];            // register column | swizzled << 16
     __shared__ uint64_t RG[kMaxRounds][4];             // global offset of register slot
     __shared__ int32_t OPS[kMaxPassOps];
+    __shared__ uint64_t CST[4];
     const int tid = threadIdx.x;
     if (tid == 0) P = kp.passes[pass_idx];
     __syncthreads();
@@ -162,7 +163,8 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
             const DevRound &R = RR[r];
             if (r == 0) cp_async_wait_all();
             __syncthreads();
-            if (R.term_count > 0) {
+            const bool has_cst = (R.cst_count[0] | R.cst_count[1] | R.cst_count[2] | R.cst_count[3]) != 0;
+            if (R.term_count > 0 || has_cst) {
                 for (int j = tid; j < R.term_count; j += NT) {
                     const int g = R.term_begin + j;
                     const uint64_t q = (uint64_t)__ldg(kp.term_q + g);
@@ -172,6 +174,12 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
                     t.pad = 0;
                     ST[j] = t;
                 }
+                for (int c = warp; c < 4; c += NW)
+                    if (R.cst_count[c] > 0) {
+                        const uint64_t v = warp_const_sum(xo, kp.cst_mo, kp.cst_q, R.cst_begin[c],
+                                                          R.cst_count[c], lane);
+                        if (lane == 0) CST[c] = v;
+                    }
                 __syncthreads();
             }
             const uint32_t v = LTL[r][lane] ^ LTW[r][warp];
@@ -308,9 +316,11 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
                     break;
                 }
                 default:
-                    if ((code & 7) == D_DIAG)
-                        diag_apply(a, lf, kp.diags[code >> 9], ST, TW,
-                                   ((code >> 5) & 1) ? diag_scale : (T)1);
+                    if ((code & 7) == D_DIAG) {
+                        const DevDiag &dg = kp.diags[code >> 9];
+                        diag_apply(a, lf, dg, ST, TW, ((code >> 5) & 1) ? diag_scale : (T)1,
+                                   dg.cst >= 0 ? CST[dg.cst] : (uint64_t)0);
+                    }
                     break;
                 }
             }
@@ -392,7 +402,7 @@ cudaError_t run_tile(void *psi, int n, const DevSchedule &S, int pass, int num_s
     if (e != cudaSuccess) return e;
     if (b < 1) b = 1;
     KParams kp{S.passes, S.rounds, S.ops, S.perms, S.diags, S.phases,
-               S.term_mo, S.term_ml, S.term_q, S.mask_pool, S.c};
+               S.term_mo, S.term_ml, S.term_q, S.mask_pool, S.cst_mo, S.cst_q, S.c};
     int64_t ntiles = (int64_t)1 << (n - K);
     int64_t grid = (int64_t)num_sms * b;
     if (grid > ntiles) grid = ntiles;

@@ -22,6 +22,8 @@ struct DevSchedule {
     uint32_t *term_ml = nullptr;
     int64_t *term_q = nullptr;
     uint64_t *mask_pool = nullptr;
+    uint64_t *cst_mo = nullptr;
+    int64_t *cst_q = nullptr;
     std::vector<DevPass> host_passes;  // for launch-side decisions
 };
 

@@ -419,7 +419,9 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
         for (;;) {
             bool is_load = nr == 0;
             // -------- register positions for this round
-            std::vector<std::pair<int, int>> score;  // (first pending G1 index, position)
+            // score: (first pending one-qubit op on the position, or INT32_MAX if
+            // none is ready -- all its predecessors done -- yet)
+            std::vector<std::pair<int, int>> score;
             for (int p = 0; p < K; p++) {
                 if (is_load && p < c) continue;
                 int best = INT32_MAX;
@@ -427,7 +429,10 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                     if (done[j] >= 0) continue;
                     const FlatOp &op = circ.ops[j];
                     if (is_1q(op.kind) && op.q == tq[p]) {
-                        best = j;
+                        bool ready = true;
+                        for (int pr : preds[j])
+                            if (done[pr] < 0) { ready = false; break; }
+                        if (ready) best = j;
                         break;
                     }
                 }
@@ -436,7 +441,26 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             std::stable_sort(score.begin(), score.end());
             DevRound R{};
             std::vector<int> regs;
-            for (int i = 0; i < 4; i++) regs.push_back(score[i].second);
+            // The low positions (< c) are lanes in the load and store layouts, so
+            // their gates need a middle round: when one of them is due, take all
+            // low positions with pending gates together, then the most urgent others.
+            // Low positions are taken all together or not at all, and before the
+            // last high positions so that the final round can also store.
+            int lows_pending = 0, highs_pending = 0;
+            for (auto &sc : score)
+                if (sc.first != INT32_MAX) (sc.second < c ? lows_pending : highs_pending)++;
+            const bool low_round = !is_load && lows_pending > 0 &&
+                                   ((score[0].first != INT32_MAX && score[0].second < c) || highs_pending <= 4);
+            if (low_round)
+                for (auto &sc : score)
+                    if (sc.second < c && sc.first != INT32_MAX && (int)regs.size() < 4) regs.push_back(sc.second);
+            for (auto &sc : score)
+                if ((int)regs.size() < 4 && sc.second >= c &&
+                    std::find(regs.begin(), regs.end(), sc.second) == regs.end())
+                    regs.push_back(sc.second);
+            for (auto &sc : score)   // only if fewer than 4 high positions exist
+                if ((int)regs.size() < 4 && std::find(regs.begin(), regs.end(), sc.second) == regs.end())
+                    regs.push_back(sc.second);
             std::sort(regs.begin(), regs.end());
             for (int i = 0; i < 4; i++) R.reg_pos[i] = (uint8_t)regs[i];
             R.perm = -1;
@@ -539,12 +563,28 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                             cls[u].push_back((int)t);
                         }
                         DevDiag dd{};
+                        dd.cst = -1;
                         int off = (int)S.term_q.size() - R.term_begin;
-                        uint64_t outer_mask = 0;
+                        uint64_t outer_mask = 0, tile_mask = 0;
                         for (int k = 0; k < no; k++) outer_mask |= uint64_t(1) << P.outer_bits[k];
+                        for (int p = 0; p < K; p++) tile_mask |= uint64_t(1) << tq[p];
+                        int slot = -1;
+                        for (int c2 = 0; c2 < 4; c2++)
+                            if (R.cst_count[c2] == 0) { slot = c2; break; }
+                        if (slot >= 0) {
+                            R.cst_begin[slot] = (int)S.cst_q.size();
+                            for (int t : cls[0])
+                                if (!(D.masks[t] & tile_mask)) {
+                                    S.cst_mo.push_back(D.masks[t]);
+                                    S.cst_q.push_back(D.q[t]);
+                                }
+                            R.cst_count[slot] = (int)S.cst_q.size() - R.cst_begin[slot];
+                            if (R.cst_count[slot] > 0) dd.cst = slot;
+                        }
                         for (int s = 0; s < 16; s++) {
                             dd.off[s] = off;
                             for (int t : cls[s]) {
+                                if (dd.cst >= 0 && s == 0 && !(D.masks[t] & tile_mask)) continue;
                                 uint32_t ml = 0;
                                 for (int p = 0; p < K; p++)
                                     if (!((regmask >> tq[p]) & 1) && ((D.masks[t] >> tq[p]) & 1))

@@ -163,7 +163,7 @@ __device__ __forceinline__ double2 rotate_tw(double2 a, uint64_t t, const double
 template <typename A, typename T>
 __device__ __forceinline__ void diag_apply(A *a, uint32_t lf, const DevDiag &d,
                                            const StagedTerm *__restrict__ st,
-                                           const A *__restrict__ tw, T sc) {
+                                           const A *__restrict__ tw, T sc, uint64_t g0) {
     uint64_t G[16];
 #pragma unroll
     for (int s = 0; s < 16; s++) {
@@ -181,6 +181,7 @@ __device__ __forceinline__ void diag_apply(A *a, uint32_t lf, const DevDiag &d,
         }
         G[s] = acc0 + acc1;
     }
+    G[0] += g0;
     wht16(G);
 #pragma unroll
     for (int s = 0; s < 16; s++) a[s] = rotate_tw(a[s], G[s], tw, sc);
@@ -219,6 +220,21 @@ __device__ __forceinline__ void phase_apply(A *a, uint64_t xf, const int *gq, co
 }
 
 
+
+// Signed sum over a warp's strided share of `count` tile-constant terms,
+// reduced across the warp (every lane returns the total).
+__device__ __forceinline__ uint64_t warp_const_sum(uint64_t xo, const uint64_t *__restrict__ mo,
+                                                   const int64_t *__restrict__ q, int begin, int count,
+                                                   int lane) {
+    uint64_t acc = 0;
+    for (int j = lane; j < count; j += 32) {
+        const uint64_t v = (uint64_t)__ldg(q + begin + j);
+        acc += (__popcll(xo & __ldg(mo + begin + j)) & 1) ? (0 - v) : v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    return acc;
+}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
