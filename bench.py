@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--pauli-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip per-Pauli / c128 / e2e legs")
-    ap.add_argument("--n-override", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--qubits", type=int, default=30, choices=[16, 20, 24, 25, 28, 30],
+                    help="lattice size: 30 is the benchmark workload (5x6); smaller lattices "
+                         "are for profiler captures")
     return ap.parse_args()
 
 
@@ -132,12 +134,12 @@ def barrier(ws):
         dist.barrier()
 
 
-def workload(n_override=0):
+LATTICES = {16: (4, 4), 20: (4, 5), 24: (4, 6), 25: (5, 5), 28: (4, 7), 30: (5, 6)}
+
+
+def workload(qubits=30):
     from workloads import heisenberg_lattice, neel_index
-    if n_override:
-        rows = {16: (4, 4), 20: (4, 5), 24: (4, 6), 25: (5, 5), 30: (5, 6)}[n_override]
-    else:
-        rows = (5, 6)
+    rows = LATTICES[qubits]
     h = heisenberg_lattice(*rows)
     return h, neel_index(*rows), f"heisenberg_{rows[0]}x{rows[1]}_n{h.n}"
 
@@ -145,17 +147,18 @@ def workload(n_override=0):
 DT = 0.02
 
 
-def cpu_oracle_sample(h, budget_s=15.0):
+def cpu_oracle_sample(h, neel, budget_s=15.0, psi=None):
     """Oracle (one rotation at a time, complex128, OpenMP on the host cores)
     on a bounded sample of one Trotter step: the first k rotations of the
-    grouped order, timed and scaled to the step's m rotations."""
+    grouped order, timed and scaled to the step's m rotations.  psi (the
+    2^n host state) is reused when given."""
     import oracle
     from oracle import planner as P
-    from workloads import neel_index
     groups = P.greedy_partition(h.x, h.z)
     seq = [j for g in groups for j in g]
-    psi = np.zeros(1 << h.n, dtype=np.complex128)
-    psi[neel_index(5, 6) if h.n == 30 else 0] = 1.0
+    if psi is None:
+        psi = np.zeros(1 << h.n, dtype=np.complex128)
+        psi[neel] = 1.0
     t0 = time.perf_counter()
     j = seq[0]
     psi = _oracle_rot_inplace(oracle, psi, h, j)
@@ -184,12 +187,14 @@ def run_reference(args):
     ws, rank, _ = dist_init() if int(os.environ.get("WORLD_SIZE", "1")) > 1 else (1, 0, 0)
     if rank != 0:
         return
-    h, _, name = workload(args.n_override)
+    h, neel, name = workload(args.qubits)
     vals = []
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     info = None
+    psi = np.zeros(1 << h.n, dtype=np.complex128)
+    psi[neel] = 1.0
     for i in range(args.warmup + args.steps):
-        info = cpu_oracle_sample(h, budget_s=budget)
+        info = cpu_oracle_sample(h, neel, budget_s=budget, psi=psi)
         if i >= args.warmup:
             vals.append(info["value"])
     v = float(np.mean(vals))
@@ -214,7 +219,7 @@ def main():
     ws, rank, local = dist_init()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    h, neel, name = workload(args.n_override)
+    h, neel, name = workload(args.qubits)
     n = h.n
     sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
     st64 = sim.schedule_stats(sd.C64, 1)
@@ -323,7 +328,7 @@ def main():
         del host, dst, back
         torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_oracle_sample(h)
+        out["cpu_baseline"] = cpu_oracle_sample(h, neel)
     if rank == 0:
         print(json.dumps(out))
 

@@ -150,6 +150,11 @@ std::string thread_expr(const DevRound &R, int K, const std::function<uint64_t(i
     return o.str();
 }
 
+// Generated kernel of pass pi: sd_pass_c64_<pi> or sd_pass_c128_<pi>.
+std::string kernel_name(int pi, bool dbl_state) {
+    return std::string(dbl_state ? "sd_pass_c128_" : "sd_pass_c64_") + std::to_string(pi);
+}
+
 std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     const DevPass &P = S.passes[pi];
     const int K = S.K, c = S.c;
@@ -170,7 +175,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     const bool table_scaled = P.scale_in_diag && n_diag == 1;
     const double table_scale = table_scaled ? P.scale : 1.0;
     std::ostringstream o;
-    o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") sdp_" << pi
+    o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << kernel_name(pi, dbl_state)
       << "(A *__restrict__ psi, sd::KParams kp) {\n"
       << "  using namespace sd;\n"
       << "  constexpr int K = " << K << ", NT = " << NT << ", E = " << E << ";\n"
@@ -460,7 +465,7 @@ std::string jit_build(const Schedule &S, int n, bool dbl_state, JitProgram &out)
     out.K = S.K;
     for (int p = 0; p < (int)S.passes.size(); p++) {
         CUfunction f = nullptr;
-        const std::string name = "sdp_" + std::to_string(p);
+        const std::string name = kernel_name(p, dbl_state);
         if (g_drv.get_function(&f, mod, name.c_str()) != CUDA_SUCCESS) return "missing kernel " + name;
         const size_t amp = dbl_state ? 16 : 8;
         const size_t smem = 2 * (amp << S.K) + sizeof(StagedTerm) *
