@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--pauli-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip per-Pauli / c128 / e2e legs")
+    ap.add_argument("--workload", default="heisenberg30",
+                    choices=["heisenberg30", "heisenberg32", "tfim10", "batch", "jw26", "grad24"],
+                    help="heisenberg30 is the benchmark line; the others measure the remaining "
+                         "configurations and print their own line")
     ap.add_argument("--qubits", type=int, default=30, choices=[16, 20, 24, 25, 28, 30],
                     help="lattice size: 30 is the benchmark workload (5x6); smaller lattices "
                          "are for profiler captures")
@@ -213,6 +217,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "heisenberg30":
+        import bench_workloads
+        return bench_workloads.run(args)
     import torch
     import paper_2206_11664_gb300 as sd
 

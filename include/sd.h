@@ -74,7 +74,7 @@ typedef struct {
     int tile_bits;
     /* Run-time specialisation of the tile passes (each pass compiled with
      * NVRTC for sm_103a, cached in memory and under $SD_JIT_CACHE or
-     * ~/.cache/sd_jit): 0 = automatic (states of 20+ qubits with at most 128
+     * ~/.cache/sd_jit): 0 = automatic (states of 20+ qubits with at most 512
      * passes per program), 1 = always on the tile path, -1 = never.  Falls
      * back to the precompiled interpreter kernel if NVRTC is unavailable. */
     int jit;
@@ -176,8 +176,12 @@ sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt,
                   double *grad_out, void *cuda_stream);
 
 /* Evolve `count` independent problems (each its own planned context and
- * device state, qubit counts may differ) with the same dt/steps/order,
- * as one CUDA graph launch per call. */
+ * device state; qubit counts may differ) with the same dt/steps/order.
+ * Problems whose states fit one block's shared memory run in one launch
+ * each; the others are grouped by tile size and advanced pass level by pass
+ * level, one launch per level covering every problem of the group, with the
+ * blocks of a launch shared among the problems in proportion to their
+ * sizes.  Asynchronous on the stream; at most 65535 problems. */
 sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t count,
                           sd_dtype dtype, double dt, int64_t steps, int order,
                           void *cuda_stream);

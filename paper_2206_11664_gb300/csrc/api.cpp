@@ -136,7 +136,8 @@ int default_tile_bits(const sd_ctx *ctx, bool dbl) {
 bool use_onchip(const sd_ctx *ctx, bool dbl) { return ctx->n <= onchip_max_qubits(dbl); }
 
 // Build and upload a program for a circuit.
-sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &P) {
+sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &P,
+                        bool allow_jit = true) {
     P.onchip = use_onchip(ctx, dbl);
     Circuit circ = circ_in;
     canonicalize_1q(circ, ctx->n);
@@ -205,7 +206,9 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
     P.diag_passes = S.diag_passes;
     int mode = ctx->jit_opt;
     if (const char *e = getenv("SD_JIT")) mode = atoi(e) > 0 ? 1 : (e[0] == '0' ? -1 : mode);
-    const bool want = mode > 0 || (mode == 0 && n >= 20 && P.passes <= 128);
+    // one-shot programs (the half steps that open and close a second-order
+    // evolution) are not worth a compilation unless specialisation is forced
+    const bool want = mode > 0 || (mode == 0 && allow_jit && n >= 20 && P.passes <= 512);
     if (want && P.passes > 0) {
         std::string why = jit_build(S, n, dbl, P.jit);
         if (!why.empty()) {
@@ -268,7 +271,7 @@ sd_status get_program(sd_ctx *ctx, bool dbl, int order, int kind, double dt, Pro
     }
     auto P = std::make_unique<Program>();
     Circuit c = segment_circuit(ctx, order, kind, dt);
-    sd_status s = build_program(ctx, c, dbl, *P);
+    sd_status s = build_program(ctx, c, dbl, *P, kind == 0 || kind == 2);
     if (s != SD_OK) {
         free_program(*P);
         return s;
@@ -819,15 +822,107 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
                           double dt, int64_t steps, int order, void *cuda_stream) {
     sd_ctx *ctx = nullptr;
     if (!ctxs || !d_states || count < 0) return fail(nullptr, SD_EINVAL, "invalid batch arguments");
+    if (count > 65535) return fail(nullptr, SD_EINVAL, "at most 65535 instances per batch");
+    if (steps < 0 || !std::isfinite(dt)) return fail(nullptr, SD_EINVAL, "invalid steps or dt");
     for (int64_t i = 0; i < count; i++) {
         sd_status s = check_state_args(ctxs[i], d_states[i], dtype, order);
         if (s != SD_OK) return s;
     }
+    if (steps == 0 || count == 0) return SD_OK;
+    const bool dbl = dtype == SD_C128;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // Every instance's programs are built first; instances on the on-chip path
+    // run on their own (one launch each); the others are grouped by tile size
+    // and advanced level by level, one launch per level for the whole group.
+    struct Item {
+        sd_ctx *ctx;
+        void *psi;
+        Program *prog[3];
+        int64_t reps;
+    };
+    std::map<int, std::vector<Item>> by_k;
     for (int64_t i = 0; i < count; i++) {
         ctx = ctxs[i];
-        sd_status s = evolve_impl(ctx, d_states[i], dtype == SD_C128, dt, steps, order,
-                                  (cudaStream_t)cuda_stream);
-        if (s != SD_OK) return s;
+        const int G = (int)ctx->plan.groups.size();
+        Item it{ctx, d_states[i], {nullptr, nullptr, nullptr}, steps};
+        sd_status s;
+        if (order == 1 || G == 1 || steps == 1) {
+            if ((s = get_program(ctx, dbl, order, 0, dt, it.prog[1])) != SD_OK) return s;
+        } else {
+            if ((s = get_program(ctx, dbl, order, 1, dt, it.prog[0])) != SD_OK) return s;
+            if ((s = get_program(ctx, dbl, order, 2, dt, it.prog[1])) != SD_OK) return s;
+            if ((s = get_program(ctx, dbl, order, 3, dt, it.prog[2])) != SD_OK) return s;
+            it.reps = steps - 1;
+        }
+        int K = -1;
+        bool mixed = false;
+        for (Program *p : it.prog) {
+            if (!p) continue;
+            if (p->onchip) mixed = true;
+            else if (K < 0) K = p->sched.K;
+            else if (K != p->sched.K) mixed = true;
+        }
+        if (mixed || K < 0) {
+            if ((s = evolve_impl(ctx, it.psi, dbl, dt, steps, order, st)) != SD_OK) return s;
+            continue;
+        }
+        by_k[K].push_back(it);
+    }
+    for (auto &kv : by_k) {
+        const int K = kv.first;
+        std::vector<Item> &items = kv.second;
+        ctx = items[0].ctx;
+        int64_t total_tiles = 0;
+        int max_stage = 0;
+        for (auto &it : items) {
+            total_tiles += (int64_t)1 << (it.ctx->n - K);
+            for (Program *p : it.prog)
+                if (p)
+                    for (auto &ps : p->sched.host_passes) max_stage = std::max(max_stage, ps.max_stage);
+        }
+        const size_t smem = tile_pass_smem(dbl, K, max_stage);
+        if (smem > tile_pass_smem_limit()) return fail(ctx, SD_EINTERNAL, "batch pass needs too much shared memory");
+        const int occ = tile_pass_batch_occupancy(dbl, K, smem);
+        const int64_t target = (int64_t)ctx->num_sms * occ * 2;
+        std::vector<BatchInstance> inst(items.size());
+        std::vector<uint16_t> cta;
+        int64_t max_levels = 0;
+        for (size_t i = 0; i < items.size(); i++) {
+            const Item &it = items[i];
+            const int64_t tiles = (int64_t)1 << (it.ctx->n - K);
+            int64_t c = (target * tiles + total_tiles - 1) / total_tiles;
+            c = std::max<int64_t>(1, std::min(c, tiles));
+            BatchInstance &B = inst[i];
+            B.psi = it.psi;
+            B.n = it.ctx->n;
+            B.cta_begin = (int)cta.size();
+            B.cta_count = (int)c;
+            B.reps_core = it.reps;
+            for (int k = 0; k < 3; k++) {
+                Program *p = it.prog[k];
+                B.npass[k] = p ? (int)p->sched.n_passes : 0;
+                if (p)
+                    B.kp[k] = KParams{p->sched.passes, p->sched.rounds, p->sched.ops, p->sched.perms,
+                                      p->sched.diags, p->sched.phases, p->sched.term_mo, p->sched.term_ml,
+                                      p->sched.term_q, p->sched.mask_pool, p->sched.cst_mo,
+                                      p->sched.cst_q, p->sched.c};
+                else
+                    B.kp[k] = KParams{};
+            }
+            B.levels = (int64_t)B.npass[0] + (int64_t)B.npass[1] * B.reps_core + B.npass[2];
+            max_levels = std::max(max_levels, B.levels);
+            for (int64_t j = 0; j < c; j++) cta.push_back((uint16_t)i);
+        }
+        BatchInstance *d_inst = nullptr;
+        uint16_t *d_cta = nullptr;
+        CK(cudaMallocAsync((void **)&d_inst, sizeof(BatchInstance) * inst.size(), st));
+        CK(cudaMallocAsync((void **)&d_cta, sizeof(uint16_t) * cta.size(), st));
+        CK(cudaMemcpyAsync(d_inst, inst.data(), sizeof(BatchInstance) * inst.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_cta, cta.data(), sizeof(uint16_t) * cta.size(), cudaMemcpyHostToDevice, st));
+        for (int64_t L = 0; L < max_levels; L++)
+            CK(launch_tile_pass_batch(dbl, K, d_inst, d_cta, (int)cta.size(), smem, L, st));
+        CK(cudaFreeAsync(d_inst, st));
+        CK(cudaFreeAsync(d_cta, st));   // pageable-source copies are staged before they return
     }
     return SD_OK;
 }

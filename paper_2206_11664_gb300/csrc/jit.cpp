@@ -22,6 +22,9 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <atomic>
+#include <thread>
+#include <algorithm>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -407,13 +410,17 @@ bool jit_available(std::string *why) {
     return g_nvrtc.ok && g_drv.ok;
 }
 
-std::string jit_source(const Schedule &S, int n, bool dbl_state) {
+std::string source_range(const Schedule &S, int n, bool dbl_state, int first, int last) {
     std::ostringstream src;
     src << "#include \"dev_types.h\"\n#include \"tile_device.cuh\"\n"
         << "typedef " << (dbl_state ? "double" : "float") << " T;\n"
         << "typedef " << (dbl_state ? "double2" : "float2") << " A;\n\n";
-    for (int p = 0; p < (int)S.passes.size(); p++) src << gen_pass(S, p, n, dbl_state);
+    for (int p = first; p < last; p++) src << gen_pass(S, p, n, dbl_state);
     return src.str();
+}
+
+std::string jit_source(const Schedule &S, int n, bool dbl_state) {
+    return source_range(S, n, dbl_state, 0, (int)S.passes.size());
 }
 
 std::string jit_compile_check(const std::string &src) {
@@ -424,49 +431,73 @@ std::string jit_compile_check(const std::string &src) {
     return compile_cubin(src, cubin);
 }
 
+// Passes are compiled in chunks (one NVRTC program each, on a pool of host
+// threads); each chunk's cubin is cached in memory and on disk by the hash of
+// its source.
 std::string jit_build(const Schedule &S, int n, bool dbl_state, JitProgram &out) {
     std::lock_guard<std::mutex> lk(g_mu);
     init_locked();
     if (!(g_nvrtc.ok && g_drv.ok)) return g_why;
-    const std::string code = jit_source(S, n, dbl_state);
+    const int P = (int)S.passes.size();
+    const int chunk = 12;
+    const int nchunks = (P + chunk - 1) / chunk;
     int maj = 0, min = 0;
     g_nvrtc.version(&maj, &min);
-    const std::string key = std::to_string(std::hash<std::string>{}(code)) + "_" +
-                            std::to_string(code.size()) + "_nvrtc" + std::to_string(maj) + "." +
-                            std::to_string(min);
-    CUmodule mod = nullptr;
-    auto it = g_modules.find(key);
-    if (it != g_modules.end()) {
-        mod = it->second;
-    } else {
-        std::string cubin;
-        const std::string dir = cache_dir(), path = dir + "/" + key + ".cubin";
-        {
-            std::ifstream f(path, std::ios::binary);
-            if (f) cubin.assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+    std::vector<std::string> code(nchunks), key(nchunks), cubin(nchunks), err(nchunks);
+    std::vector<CUmodule> mods(nchunks, nullptr);
+    const std::string dir = cache_dir();
+    std::vector<int> todo;
+    for (int c = 0; c < nchunks; c++) {
+        code[c] = source_range(S, n, dbl_state, c * chunk, std::min(P, (c + 1) * chunk));
+        key[c] = std::to_string(std::hash<std::string>{}(code[c])) + "_" + std::to_string(code[c].size()) +
+                 "_nvrtc" + std::to_string(maj) + "." + std::to_string(min);
+        auto it = g_modules.find(key[c]);
+        if (it != g_modules.end()) {
+            mods[c] = it->second;
+            continue;
         }
-        if (cubin.empty()) {
-            std::string err = compile_cubin(code, cubin);
-            if (!err.empty()) return err;
-            mkdirs(dir);
+        std::ifstream f(dir + "/" + key[c] + ".cubin", std::ios::binary);
+        if (f) cubin[c].assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+        if (cubin[c].empty()) todo.push_back(c);
+    }
+    if (!todo.empty()) {
+        unsigned hw = std::thread::hardware_concurrency();
+        const int nthreads = (int)std::max(1u, std::min<unsigned>(hw ? hw : 4, (unsigned)todo.size()));
+        std::atomic<int> next{0};
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nthreads; t++)
+            pool.emplace_back([&]() {
+                for (int i = next++; i < (int)todo.size(); i = next++) {
+                    const int c = todo[i];
+                    err[c] = compile_cubin(code[c], cubin[c]);
+                }
+            });
+        for (auto &th : pool) th.join();
+        mkdirs(dir);
+        for (int c : todo) {
+            if (!err[c].empty()) return err[c];
+            const std::string path = dir + "/" + key[c] + ".cubin";
             const std::string tmp = path + ".tmp" + std::to_string(getpid());
             std::ofstream f(tmp, std::ios::binary);
             if (f) {
-                f.write(cubin.data(), (std::streamsize)cubin.size());
+                f.write(cubin[c].data(), (std::streamsize)cubin[c].size());
                 f.close();
                 rename(tmp.c_str(), path.c_str());
             }
         }
-        if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS) return "cuModuleLoadData failed";
-        g_modules[key] = mod;
+    }
+    for (int c = 0; c < nchunks; c++) {
+        if (mods[c]) continue;
+        if (g_drv.load(&mods[c], cubin[c].data()) != CUDA_SUCCESS) return "cuModuleLoadData failed";
+        g_modules[key[c]] = mods[c];
     }
     out = JitProgram{};
-    out.module = mod;
+    out.module = mods.empty() ? nullptr : (void *)mods[0];
     out.K = S.K;
-    for (int p = 0; p < (int)S.passes.size(); p++) {
+    for (int p = 0; p < P; p++) {
         CUfunction f = nullptr;
         const std::string name = kernel_name(p, dbl_state);
-        if (g_drv.get_function(&f, mod, name.c_str()) != CUDA_SUCCESS) return "missing kernel " + name;
+        if (g_drv.get_function(&f, mods[p / chunk], name.c_str()) != CUDA_SUCCESS) return "missing kernel " + name;
         const size_t amp = dbl_state ? 16 : 8;
         const size_t smem = 2 * (amp << S.K) + sizeof(StagedTerm) *
                                                    (size_t)(S.passes[p].max_stage > 0 ? S.passes[p].max_stage : 1);

@@ -40,8 +40,8 @@ __host__ __device__ __forceinline__ int32_t pack_op(const DevOp &o) {
 // Per-round thread layouts (tile index, swizzled index, global offset of the
 // fixed bits) come from tables built once per block.
 template <typename T, int K>
-__global__ void __launch_bounds__(1 << (K - 4))
-tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KParams kp) {
+__device__ __forceinline__ void tile_pass_body(typename VT<T>::A *__restrict__ psi, int n, int pass_idx,
+                                               const KParams &kp, int64_t first_tile, int64_t tile_stride) {
     using A = typename VT<T>::A;
     constexpr int NT = 1 << (K - 4);
     constexpr int NW = NT / 32;
@@ -154,9 +154,9 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
         cp_async_commit();
     };
 
-    int64_t tile = blockIdx.x;
+    int64_t tile = first_tile;
     if (tile < ntiles) prefetch(tile);
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (; tile < ntiles; tile += tile_stride) {
         const uint64_t xo = deposit(tile);
         A a[16];
         for (int r = 0; r < nr; r++) {
@@ -201,7 +201,7 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
                     a[s] = Pf[l];
                 }
                 __syncthreads();
-                if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
+                if (tile + tile_stride < ntiles) prefetch(tile + tile_stride);
             } else {
 #pragma unroll
                 for (int s = 0; s < 16; s++) {
@@ -375,6 +375,35 @@ tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KPara
             }
         }
     }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(1 << (K - 4))
+tile_pass_kernel(typename VT<T>::A *__restrict__ psi, int n, int pass_idx, KParams kp) {
+    tile_pass_body<T, K>(psi, n, pass_idx, kp, blockIdx.x, gridDim.x);
+}
+
+// Level-synchronous batch: block b serves instance cta_inst[b]; at `level`
+// that instance runs pass f(level) of its head / core / tail programs.
+template <typename T, int K>
+__global__ void __launch_bounds__(1 << (K - 4))
+tile_pass_batch_kernel(const BatchInstance *__restrict__ inst, const uint16_t *__restrict__ cta_inst,
+                       int64_t level) {
+    const BatchInstance &I = inst[cta_inst[blockIdx.x]];
+    if (level >= I.levels) return;
+    int prog, pass;
+    if (level < I.npass[0]) {
+        prog = 0;
+        pass = (int)level;
+    } else if (level - I.npass[0] < (int64_t)I.npass[1] * I.reps_core) {
+        prog = 1;
+        pass = (int)((level - I.npass[0]) % I.npass[1]);
+    } else {
+        prog = 2;
+        pass = (int)(level - I.npass[0] - (int64_t)I.npass[1] * I.reps_core);
+    }
+    tile_pass_body<T, K>(reinterpret_cast<typename VT<T>::A *>(I.psi), I.n, pass, I.kp[prog],
+                         (int64_t)blockIdx.x - I.cta_begin, I.cta_count);
 }
 
 struct OccCache {
@@ -741,6 +770,59 @@ grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restr
 
 
 }  // namespace
+
+template <typename T, int K>
+cudaError_t run_batch(const BatchInstance *d_inst, const uint16_t *d_cta, int blocks, size_t smem,
+                      int64_t level, cudaStream_t st) {
+    static bool init = false;
+    if (!init) {
+        cudaError_t e = cudaFuncSetAttribute(tile_pass_batch_kernel<T, K>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tile_smem_limit());
+        if (e != cudaSuccess) return e;
+        init = true;
+    }
+    tile_pass_batch_kernel<T, K><<<blocks, 1 << (K - 4), smem, st>>>(d_inst, d_cta, level);
+    return cudaGetLastError();
+}
+
+int tile_pass_batch_occupancy(bool dbl, int K, size_t smem) {
+    int b = 0;
+    const int threads = 1 << (K - 4);
+#define SD_OCC_CASE(KK)                                                                            \
+    case KK:                                                                                       \
+        if (dbl) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tile_pass_batch_kernel<double, KK>, threads, smem); \
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tile_pass_batch_kernel<float, KK>, threads, smem);     \
+        break;
+    switch (K) {
+        SD_OCC_CASE(9)
+        SD_OCC_CASE(10)
+        SD_OCC_CASE(11)
+        SD_OCC_CASE(12)
+        SD_OCC_CASE(13)
+    default: break;
+    }
+#undef SD_OCC_CASE
+    cudaGetLastError();
+    return b > 0 ? b : 1;
+}
+
+cudaError_t launch_tile_pass_batch(bool dbl, int K, const BatchInstance *d_inst, const uint16_t *d_cta_inst,
+                                   int blocks, size_t smem, int64_t level, cudaStream_t st) {
+#define SD_BATCH_CASE(KK)                                                                         \
+    case KK:                                                                                      \
+        return dbl ? run_batch<double, KK>(d_inst, d_cta_inst, blocks, smem, level, st)          \
+                   : run_batch<float, KK>(d_inst, d_cta_inst, blocks, smem, level, st);
+    switch (K) {
+        SD_BATCH_CASE(9)
+        SD_BATCH_CASE(10)
+        SD_BATCH_CASE(11)
+        SD_BATCH_CASE(12)
+        SD_BATCH_CASE(13)
+    default: return cudaErrorInvalidValue;
+    }
+#undef SD_BATCH_CASE
+}
 
 size_t tile_pass_smem(bool dbl, int K, int max_stage) {
     const size_t amp = dbl ? 16 : 8;

@@ -44,6 +44,26 @@ struct DevCircuit {
     uint64_t *phase_up = nullptr;                         // n per phase layer
 };
 
+// One instance of a level-synchronous batch: at level L it runs the L-th pass
+// of its sequence head (npass[0] passes), core x reps_core, tail (npass[2]),
+// on blocks [cta_begin, cta_begin + cta_count) of the launch.
+struct BatchInstance {
+    void *psi;
+    int n;
+    int cta_begin, cta_count;
+    int npass[3];
+    int64_t reps_core;
+    int64_t levels;
+    KParams kp[3];
+};
+
+// Launch level `level` of a batch whose instances all use tile size K;
+// cta_inst maps each block to its instance; smem = the largest pass need.
+cudaError_t launch_tile_pass_batch(bool dbl, int K, const BatchInstance *d_inst, const uint16_t *d_cta_inst,
+                                   int blocks, size_t smem, int64_t level, cudaStream_t st);
+
+int tile_pass_batch_occupancy(bool dbl, int K, size_t smem);
+
 // Dynamic shared memory of a tile pass and its limit.
 size_t tile_pass_smem(bool dbl, int K, int max_stage);
 size_t tile_pass_smem_limit();

@@ -202,6 +202,23 @@ def test_gradient_autograd_function(sd):
     assert np.max(np.abs(c.grad.numpy() - g_ref)) < 1e-9
 
 
+@pytest.mark.parametrize("dtype,order", [("c64", 2), ("c128", 1), ("c128", 2)])
+def test_batch_levels_match_oracle(sd, dtype, order):
+    """Tile-path problems of different sizes advanced level by level in shared
+    launches (plus one on-chip problem), against the oracle."""
+    rng = np.random.default_rng(91 + order)
+    sims, states, refs = [], [], []
+    for n in (14, 17, 15, 11, 16):
+        h = random_klocal(n, 40, rng, weights=(2, 3))
+        psi = product_state(haar_product_factors(n, rng))
+        sims.append(sd.Simulator(h.n, h.x, h.z, h.c).plan())
+        states.append(_dev(psi, dtype))
+        refs.append(oracle.evolve(h, psi, 0.01, 3, order))
+    sd.evolve_batch(sims, states, 0.01, 3, order)
+    for t, r in zip(states, refs):
+        assert np.linalg.norm(_host(t) - r) < TOL[dtype]
+
+
 def test_batch_matches_individual(sd):
     rng = np.random.default_rng(90)
     sims, states, refs = [], [], []
