@@ -150,6 +150,11 @@ def workload(qubits=30):
 
 DT = 0.02
 
+# DRAM bytes (read + write) per tile-pass launch from ncu: 4.235 GB per launch
+# at n = 28 (mean of the 7 passes of a step), scaled by the 4x tile count to
+# n = 30.  Taken on the pass kernels as they stand; re-captured when they change.
+TRAFFIC_PER_LAUNCH = {28: 4.235e9, 30: 16.94e9}
+
 
 def cpu_oracle_sample(h, neel, budget_s=15.0, psi=None):
     """Oracle (one rotation at a time, complex128, OpenMP on the host cores)
@@ -274,8 +279,9 @@ def main():
                       "parallelism": f"replicas x{ws}", "tile_bits": st64["tile_bits"],
                       "passes_per_step": passes},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": None,
-                        "kernel": "tile_pass_kernel<float,13>",
+                        "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(n),
+                        "kernel": "sd_pass_c64_* (one generated kernel per tile pass, "
+                                  f"{passes} per step; achieved = mean over the step's launches)",
                         "peak_kind": f"{peak_kind} copy bandwidth",
                         "bytes_per_launch": bytes_per_pass},
            "gpu_launches": launches,
