@@ -135,6 +135,20 @@ sd_status sd_get_plan(const sd_ctx *ctx, sd_plan_view *out);
  * and Trotter order (1 or 2).  Host only. */
 sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_stats *out);
 
+/* Builds, without launching anything, every program that
+ * sd_evolve(ctx, ., dtype, dt, steps, order, .) runs: pass schedules, their
+ * device tables and the kernels compiled at run time.  A later sd_evolve
+ * with the same arguments then starts launching at once.  Synchronous;
+ * SD_EINVAL / SD_ENOPLAN as for sd_evolve. */
+sd_status sd_prepare(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order);
+
+/* Number of tile-pass kernels sd_evolve(ctx, ., dtype, ., steps, order, .)
+ * launches; each reads and writes the state once.  0 when the state stays
+ * on chip (one launch then runs every step).  A call of several steps merges
+ * up to 4 steps (first order) or cores (second order) into one pass schedule,
+ * so this is not steps times sd_get_schedule's passes_per_step.  Host only. */
+sd_status sd_count_passes(sd_ctx *ctx, sd_dtype dtype, int order, int64_t steps, int64_t *out);
+
 /* Trotter evolution in place (Eq. trotter_simul_diag): `steps` steps of
  * size dt of order 1 (groups 1..G) or 2 (Strang: groups 1..G-1 at dt/2, G
  * at dt, G-1..1 at dt/2; the half steps of group 1 that meet between

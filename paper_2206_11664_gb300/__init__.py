@@ -156,6 +156,18 @@ class Simulator:
                 "rounds_per_step": s.rounds_per_step, "diag_passes": s.diag_passes,
                 "onchip": bool(s.onchip)}
 
+    def prepare(self, dtype, dt, steps, order=1):
+        """Build (no launch) the programs evolve(., dt, steps, order) runs on
+        a state of `dtype` (C64 / C128), including run-time compiled kernels."""
+        self._check(self._lib.sd_prepare(self._h, dtype, float(dt), int(steps), int(order)))
+        return self
+
+    def count_passes(self, dtype=C64, order=1, steps=1):
+        """Tile-pass launches evolve() makes for `steps` steps (0 on chip)."""
+        out = ctypes.c_int64(0)
+        self._check(self._lib.sd_count_passes(self._h, dtype, order, int(steps), ctypes.byref(out)))
+        return out.value
+
     # ------------------------------------------------------------ dynamics
     def evolve(self, state, dt, steps, order=1, stream=None):
         """In place: `steps` Trotter steps of size dt (order 1 or 2)."""

@@ -135,6 +135,41 @@ int default_tile_bits(const sd_ctx *ctx, bool dbl) {
 
 bool use_onchip(const sd_ctx *ctx, bool dbl) { return ctx->n <= onchip_max_qubits(dbl); }
 
+// Most tile passes of one program compiled at run time (per-pass kernels).
+constexpr int64_t kJitMaxPasses = 512;
+// Steps (first order) or cores (second order) merged into one block program.
+constexpr int kBlockSteps = 4;
+
+// Appends circuit b to circuit a (table indices of b's diagonal ops rebased).
+void append_circuit(Circuit &a, const Circuit &b) {
+    const int32_t np = (int32_t)a.phases.size(), nd = (int32_t)a.diags.size();
+    for (FlatOp op : b.ops) {
+        if (op.kind == OK_PHASE) op.idx += np;
+        else if (op.kind == OK_DIAG) op.idx += nd;
+        a.ops.push_back(op);
+    }
+    a.phases.insert(a.phases.end(), b.phases.begin(), b.phases.end());
+    a.diags.insert(a.diags.end(), b.diags.begin(), b.diags.end());
+}
+
+// Pass schedule of a canonicalised circuit on the tile path: the default
+// tile size, or smaller tiles when a pass's staged terms do not fit beside
+// the tile in shared memory.
+sd_status schedule_for(sd_ctx *ctx, const Circuit &circ, bool dbl, Schedule &S) {
+    int K = default_tile_bits(ctx, dbl);
+    const int c = dbl ? 3 : 4;
+    for (;;) {
+        std::string e = schedule_circuit(circ, ctx->n, K, c, S);
+        if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
+        size_t need = 0;
+        for (auto &p : S.passes) need = std::max(need, pass_smem_bytes(p, dbl ? 16 : 8, K));
+        if (need <= kTileSmemLimit) return SD_OK;
+        if (K <= kRegBits + kLaneBits)
+            return fail(ctx, SD_EINVAL, "a commuting group has too many terms for one tile pass");
+        K--;   // smaller tiles leave room to stage the group's terms
+    }
+}
+
 // Build and upload a program for a circuit.
 sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &P,
                         bool allow_jit = true) {
@@ -172,18 +207,8 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
         return SD_OK;
     }
     Schedule S;
-    int K = default_tile_bits(ctx, dbl);
-    int c = dbl ? 3 : 4;
-    for (;;) {
-        std::string e = schedule_circuit(circ, n, K, c, S);
-        if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
-        int ms = 0;
-        for (auto &p : S.passes) ms = std::max(ms, p.max_stage);
-        if (tile_pass_smem(dbl, K, ms) <= tile_pass_smem_limit()) break;
-        if (K <= kRegBits + kLaneBits)
-            return fail(ctx, SD_EINVAL, "a commuting group has too many terms for one tile pass");
-        K--;   // smaller tiles leave room to stage the group's terms
-    }
+    sd_status ss = schedule_for(ctx, circ, dbl, S);
+    if (ss != SD_OK) return ss;
     DevSchedule &D = P.sched;
     D.K = S.K;
     D.c = S.c;
@@ -196,7 +221,7 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
     CK(upload(P.allocs, D.diags, S.diags));
     CK(upload(P.allocs, D.phases, S.phases));
     CK(upload(P.allocs, D.term_mo, S.term_mo));
-    CK(upload(P.allocs, D.term_ml, S.term_ml));
+    CK(upload(P.allocs, D.slots, S.slots));
     CK(upload(P.allocs, D.term_q, S.term_q));
     CK(upload(P.allocs, D.mask_pool, S.mask_pool));
     CK(upload(P.allocs, D.cst_mo, S.cst_mo));
@@ -208,7 +233,7 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
     if (const char *e = getenv("SD_JIT")) mode = atoi(e) > 0 ? 1 : (e[0] == '0' ? -1 : mode);
     // one-shot programs (the half steps that open and close a second-order
     // evolution) are not worth a compilation unless specialisation is forced
-    const bool want = mode > 0 || (mode == 0 && allow_jit && n >= 20 && P.passes <= 512);
+    const bool want = mode > 0 || (mode == 0 && allow_jit && n >= 20 && P.passes <= kJitMaxPasses);
     if (want && P.passes > 0) {
         std::string why = jit_build(S, n, dbl, P.jit);
         if (!why.empty()) {
@@ -233,10 +258,22 @@ std::vector<std::pair<int, double>> step_sequence(int G, int order) {
 }
 
 // Segments of an evolution: kind 0 = one unmerged step, 1 = head, 2 = core, 3 = tail
-// (second order with half steps of group 0 merged across steps).
-Circuit segment_circuit(const sd_ctx *ctx, int order, int kind, double dt) {
+// (second order with half steps of group 0 merged across steps), 4 = block:
+// kBlockSteps (or fewer, see block_steps) repetitions of the step (first
+// order) or of the core (second order) in one program, so that the schedule
+// runs the last Clifford layer of one step in the passes of the next step's
+// first group exponential instead of in passes of its own.
+Circuit segment_circuit(const sd_ctx *ctx, int order, int kind, double dt, int reps = 1) {
     Circuit c;
     const int G = (int)ctx->plan.groups.size();
+    if (kind == 4) {
+        const int base = (order == 1 || G == 1) ? 0 : 2;
+        for (int r = 0; r < reps; r++) {
+            Circuit one = segment_circuit(ctx, order, base, dt);
+            append_circuit(c, one);
+        }
+        return c;
+    }
     auto add = [&](int g, double f) { append_group_step(ctx->plan, g, f, dt, ctx->c, c); };
     if (kind == 0 || order == 1 || G == 1) {
         for (auto &p : step_sequence(G, order)) add(p.first, p.second);
@@ -253,8 +290,8 @@ Circuit segment_circuit(const sd_ctx *ctx, int order, int kind, double dt) {
     return c;
 }
 
-sd_status get_program(sd_ctx *ctx, bool dbl, int order, int kind, double dt, Program *&out) {
-    auto key = std::make_tuple((int)dbl, order, kind, dt);
+sd_status get_program(sd_ctx *ctx, bool dbl, int order, int kind, double dt, Program *&out, int reps = 1) {
+    auto key = std::make_tuple((int)dbl, order, kind * 64 + reps, dt);
     auto it = ctx->programs.find(key);
     if (it != ctx->programs.end()) {
         out = it->second.get();
@@ -270,8 +307,8 @@ sd_status get_program(sd_ctx *ctx, bool dbl, int order, int kind, double dt, Pro
         }
     }
     auto P = std::make_unique<Program>();
-    Circuit c = segment_circuit(ctx, order, kind, dt);
-    sd_status s = build_program(ctx, c, dbl, *P, kind == 0 || kind == 2);
+    Circuit c = segment_circuit(ctx, order, kind, dt, reps);
+    sd_status s = build_program(ctx, c, dbl, *P, kind == 0 || kind == 2 || kind == 4);
     if (s != SD_OK) {
         free_program(*P);
         return s;
@@ -292,7 +329,7 @@ sd_status run_program(sd_ctx *ctx, bool dbl, Program &P, void *psi, int64_t reps
     }
     if (P.jit.ok()) {
         const KParams kp{P.sched.passes, P.sched.rounds, P.sched.ops, P.sched.perms, P.sched.diags,
-                         P.sched.phases, P.sched.term_mo, P.sched.term_ml, P.sched.term_q,
+                         P.sched.phases, P.sched.term_mo, P.sched.slots, P.sched.term_q,
                          P.sched.mask_pool, P.sched.cst_mo, P.sched.cst_q, P.sched.c};
         for (int64_t r = 0; r < reps; r++)
             for (int64_t p = 0; p < P.sched.n_passes; p++)
@@ -319,22 +356,60 @@ sd_status check_state_args(sd_ctx *ctx, const void *state, sd_dtype dtype, int o
     return ensure_device(ctx);
 }
 
+// Repetitions of a segment of `passes` tile passes merged into one block
+// program: kBlockSteps, halved until the block stays within the limit of run-time
+// compiled passes; 1 (no block) for the on-chip path.
+int block_steps(int64_t passes) {
+    if (passes <= 0) return 1;
+    int M = kBlockSteps;
+    while (M > 1 && M * passes > kJitMaxPasses) M /= 2;
+    return M;
+}
+
+// Runs `count` repetitions of the segment program R: whole blocks of M
+// repetitions through the block program, the rest through R itself.
+// (launch = false: only build the programs the call would run.)
+sd_status run_repeated(sd_ctx *ctx, bool dbl, int order, double dt, Program &R, int64_t count, void *psi,
+                       cudaStream_t st, bool launch) {
+    const int M = block_steps(R.passes);
+    if (M > 1 && count >= M) {
+        Program *B = nullptr;
+        sd_status s = get_program(ctx, dbl, order, 4, dt, B, M);
+        if (s != SD_OK) return s;
+        if (launch && (s = run_program(ctx, dbl, *B, psi, count / M, st)) != SD_OK) return s;
+        count %= M;
+    }
+    return launch ? run_program(ctx, dbl, R, psi, count, st) : SD_OK;
+}
+
 sd_status evolve_impl(sd_ctx *ctx, void *psi, bool dbl, double dt, int64_t steps, int order,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool launch = true) {
     const int G = (int)ctx->plan.groups.size();
     Program *P = nullptr;
     sd_status s;
     if (order == 1 || G == 1 || steps == 1) {
         if ((s = get_program(ctx, dbl, order, 0, dt, P)) != SD_OK) return s;
-        return run_program(ctx, dbl, *P, psi, steps, st);
+        return run_repeated(ctx, dbl, order, dt, *P, steps, psi, st, launch);
     }
     Program *H = nullptr, *C = nullptr, *T = nullptr;
     if ((s = get_program(ctx, dbl, order, 1, dt, H)) != SD_OK) return s;
     if ((s = get_program(ctx, dbl, order, 2, dt, C)) != SD_OK) return s;
     if ((s = get_program(ctx, dbl, order, 3, dt, T)) != SD_OK) return s;
-    if ((s = run_program(ctx, dbl, *H, psi, 1, st)) != SD_OK) return s;
-    if ((s = run_program(ctx, dbl, *C, psi, steps - 1, st)) != SD_OK) return s;
-    return run_program(ctx, dbl, *T, psi, 1, st);
+    if (launch && (s = run_program(ctx, dbl, *H, psi, 1, st)) != SD_OK) return s;
+    if ((s = run_repeated(ctx, dbl, order, dt, *C, steps - 1, psi, st, launch)) != SD_OK) return s;
+    return launch ? run_program(ctx, dbl, *T, psi, 1, st) : SD_OK;
+}
+
+// Tile passes of a segment's schedule, host only (0 on the on-chip path).
+sd_status segment_passes(sd_ctx *ctx, bool dbl, int order, int kind, int reps, int64_t &out) {
+    out = 0;
+    if (use_onchip(ctx, dbl)) return SD_OK;
+    Circuit c = segment_circuit(ctx, order, kind, 0.01, reps);
+    canonicalize_1q(c, ctx->n);
+    Schedule S;
+    sd_status s = schedule_for(ctx, c, dbl, S);
+    if (s == SD_OK) out = (int64_t)S.passes.size();
+    return s;
 }
 
 sd_status ensure_partial(sd_ctx *ctx, size_t count) {
@@ -673,6 +748,56 @@ sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_st
     return SD_OK;
 }
 
+sd_status sd_prepare(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order) {
+    if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
+    if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");
+    if (dtype != SD_C64 && dtype != SD_C128) return fail(ctx, SD_EINVAL, "dtype must be SD_C64 or SD_C128");
+    if (order != 1 && order != 2) return fail(ctx, SD_EINVAL, "order must be 1 or 2");
+    if (steps < 0) return fail(ctx, SD_EINVAL, "steps must be >= 0");
+    if (!std::isfinite(dt)) return fail(ctx, SD_EINVAL, "dt must be finite");
+    sd_status s = ensure_device(ctx);
+    if (s != SD_OK || steps == 0) return s;
+    return evolve_impl(ctx, nullptr, dtype == SD_C128, dt, steps, order, nullptr, false);
+}
+
+sd_status sd_count_passes(sd_ctx *ctx, sd_dtype dtype, int order, int64_t steps, int64_t *out) {
+    if (!ctx || !out) return fail(nullptr, SD_EINVAL, "null argument");
+    if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");
+    if (order != 1 && order != 2) return fail(ctx, SD_EINVAL, "order must be 1 or 2");
+    if (dtype != SD_C64 && dtype != SD_C128) return fail(ctx, SD_EINVAL, "dtype must be SD_C64 or SD_C128");
+    if (steps < 0) return fail(ctx, SD_EINVAL, "steps must be >= 0");
+    *out = 0;
+    const bool dbl = dtype == SD_C128;
+    if (steps == 0 || use_onchip(ctx, dbl)) return SD_OK;
+    const int G = (int)ctx->plan.groups.size();
+    sd_status s;
+    auto repeated = [&](int kind, int64_t count, int64_t &total) -> sd_status {
+        int64_t one = 0, blk = 0;
+        sd_status r = segment_passes(ctx, dbl, order, kind, 1, one);
+        if (r != SD_OK) return r;
+        const int M = block_steps(one);
+        if (M > 1 && count >= M) {
+            if ((r = segment_passes(ctx, dbl, order, 4, M, blk)) != SD_OK) return r;
+            total += (count / M) * blk;
+            count %= M;
+        }
+        total += count * one;
+        return SD_OK;
+    };
+    int64_t total = 0;
+    if (order == 1 || G == 1 || steps == 1) {
+        if ((s = repeated(0, steps, total)) != SD_OK) return s;
+    } else {
+        int64_t h = 0, t = 0;
+        if ((s = segment_passes(ctx, dbl, order, 1, 1, h)) != SD_OK) return s;
+        if ((s = segment_passes(ctx, dbl, order, 3, 1, t)) != SD_OK) return s;
+        if ((s = repeated(2, steps - 1, total)) != SD_OK) return s;
+        total += h + t;
+    }
+    *out = total;
+    return SD_OK;
+}
+
 sd_status sd_evolve(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt, int64_t steps, int order,
                     void *cuda_stream) {
     sd_status s = check_state_args(ctx, d_state, dtype, order);
@@ -873,15 +998,14 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
         std::vector<Item> &items = kv.second;
         ctx = items[0].ctx;
         int64_t total_tiles = 0;
-        int max_stage = 0;
+        size_t smem = 0;
         for (auto &it : items) {
             total_tiles += (int64_t)1 << (it.ctx->n - K);
             for (Program *p : it.prog)
                 if (p)
-                    for (auto &ps : p->sched.host_passes) max_stage = std::max(max_stage, ps.max_stage);
+                    for (auto &ps : p->sched.host_passes) smem = std::max(smem, pass_smem_bytes(ps, dbl ? 16 : 8, K));
         }
-        const size_t smem = tile_pass_smem(dbl, K, max_stage);
-        if (smem > tile_pass_smem_limit()) return fail(ctx, SD_EINTERNAL, "batch pass needs too much shared memory");
+        if (smem > kTileSmemLimit) return fail(ctx, SD_EINTERNAL, "batch pass needs too much shared memory");
         const int occ = tile_pass_batch_occupancy(dbl, K, smem);
         const int64_t target = (int64_t)ctx->num_sms * occ * 2;
         std::vector<BatchInstance> inst(items.size());
@@ -903,7 +1027,7 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
                 B.npass[k] = p ? (int)p->sched.n_passes : 0;
                 if (p)
                     B.kp[k] = KParams{p->sched.passes, p->sched.rounds, p->sched.ops, p->sched.perms,
-                                      p->sched.diags, p->sched.phases, p->sched.term_mo, p->sched.term_ml,
+                                      p->sched.diags, p->sched.phases, p->sched.term_mo, p->sched.slots,
                                       p->sched.term_q, p->sched.mask_pool, p->sched.cst_mo,
                                       p->sched.cst_q, p->sched.c};
                 else

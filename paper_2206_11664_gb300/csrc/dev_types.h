@@ -51,8 +51,10 @@ struct DevRound {
     int32_t op_begin, op_end;
     int32_t perm;       // -1 or index of an in-tile permutation applied on the round's smem write
     int32_t flags;      // 1: load from global, 2: store to global
-    int32_t term_begin; // group-exponential terms staged in shared memory for this round
-    int32_t term_count;
+    int32_t slot_begin; // term slots of the round's group exponentials: kp.slots[slot_begin, +slot_count)
+    int32_t slot_count;
+    int32_t diag_begin; // the round's group exponentials: kp.diags[diag_begin, +n_diag)
+    int32_t n_diag;
     // Terms whose masks meet no tile qubit of the round take one value on the
     // whole tile: their signed sum is formed once per tile into slot c
     // (pool range [cst_begin[c], cst_begin[c] + cst_count[c]) of cst_mo/cst_q).
@@ -64,7 +66,11 @@ struct DevPass {
     int32_t round_begin, n_rounds;
     int32_t n_outer;
     int32_t scale_in_diag;   // 1 if the deferred scale is folded into a D_DIAG op
-    int32_t max_stage;       // most terms staged by one round
+    int32_t max_stage;       // most term slots staged by one round
+    int32_t max_tot;         // most class totals staged by one round (16 per group exponential)
+    int32_t term_begin;      // the pass's group-exponential terms: term_mo/term_q[term_begin, +term_count)
+    int32_t term_count;
+    int32_t term_cache;      // 1: the pass copies its terms to shared memory once per block
     int32_t pad;
     double scale;            // 2^(-h/2) for h Hadamards in the pass
     uint8_t tile_bits[16];
@@ -79,12 +85,35 @@ struct DevPerm {
     uint32_t ocol[48];
 };
 
-// Per-round diagonal descriptor: terms sorted by their register projection
-// (class s = the bits of the mask on the round's 4 register positions).
-// Class s occupies [off[s], off[s+1]) of the round's staged terms.
+// Per-round diagonal descriptor.  The angle of amplitude x is
+//   T(x) = sum_j q_j (-1)^{|x & m_j|},
+// with x = (outer bits of the tile, fixed tile positions lf of the thread,
+// the 4 register bits s).  Terms are sorted by their register projection
+// (class u = the bits of m_j on the round's register positions), and within
+// a class by their mask ml on the fixed positions: the terms of one
+// (class, ml) pair form a slot, whose signed sum over the outer bits is one
+// number per tile.  Per class, G[u] = (sum of all its slots) - 2 (sum of the
+// slots whose ml has odd parity with lf); a 4-level Walsh-Hadamard
+// transform over the register bits turns G into T.
+//   off[u]..off[u+1]: the class's slots with ml != 0 (indices relative to
+//                     the round's slot_begin);
+//   zs[u]:            its slot with ml == 0, or -1;
+//   tot:              class totals live at TQ[tot + u] (tot = 16 k for the
+//                     round's k-th group exponential);
+//   cst:              tile-constant slot of the round folded into class 0, or -1.
 struct DevDiag {
     int32_t off[17];
-    int32_t cst;   // constant slot of the round holding this op's tile-constant terms, or -1
+    int32_t zs[16];
+    int32_t tot;
+    int32_t cst;
+};
+
+// A slot: terms [tb, tb + tn) of term_mo/term_q sharing a class and the mask
+// ml on the round's fixed tile positions.
+struct DevSlot {
+    int32_t tb, tn;
+    uint32_t ml;
+    int32_t pad;
 };
 
 // Per-round phase descriptor (S/CZ layer).
@@ -98,14 +127,28 @@ struct DevPhase {
 };
 
 
-// Term of a group exponential staged in shared memory for one tile: its
-// Q0.64 angle with the sign of the tile's outer bits folded in, and its mask
-// on the fixed (lane and warp) tile positions of the round.
+// A slot staged in shared memory for one tile: its Q0.64 angle sum with the
+// signs of the tile's outer bits folded in, and its mask ml.
 struct StagedTerm {
     uint64_t q;
     uint32_t ml;
     uint32_t pad;
 };
+
+// Dynamic shared memory a tile pass may use: 227 KB per block less the
+// kernels' static tables.
+constexpr size_t kTileSmemLimit = 227 * 1024 - 28 * 1024;
+// Passes with at most this many group-exponential terms keep them in shared
+// memory (16 bytes each), so that staging a tile reads no global memory.
+constexpr int kTermCache = 2048;
+
+// Dynamic shared memory of a tile pass with 2^K amplitudes of `amp` bytes per
+// tile: exchange and prefetch buffers, staged slots, class totals, and the
+// cached terms (outer masks, then angles).
+inline SD_HD size_t pass_smem_bytes(const DevPass &P, size_t amp, int K) {
+    return 2 * (amp << K) + sizeof(StagedTerm) * (size_t)(P.max_stage > 0 ? P.max_stage : 1) +
+           sizeof(uint64_t) * (size_t)P.max_tot + (P.term_cache ? 16 * (size_t)P.term_count : 0);
+}
 
 // Pointers a tile-pass kernel reads besides the state.
 struct KParams {
@@ -116,7 +159,7 @@ struct KParams {
     const DevDiag *diags;
     const DevPhase *phases;
     const uint64_t *term_mo;
-    const uint32_t *term_ml;
+    const DevSlot *slots;
     const int64_t *term_q;
     const uint64_t *mask_pool;
     const uint64_t *cst_mo;

@@ -158,6 +158,11 @@ std::string kernel_name(int pi, bool dbl_state) {
     return std::string(dbl_state ? "sd_pass_c128_" : "sd_pass_c64_") + std::to_string(pi);
 }
 
+// Whether class u of a group exponential has any term on the tile.
+bool diag_class_used(const DevDiag &d, int u) {
+    return d.off[u + 1] > d.off[u] || d.zs[u] >= 0 || (u == 0 && d.cst >= 0);
+}
+
 std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     const DevPass &P = S.passes[pi];
     const int K = S.K, c = S.c;
@@ -186,7 +191,13 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
       << "  A *X = reinterpret_cast<A *>(smraw);\n"
       << "  A *Pf = X + (1 << K);\n"
       << "  StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf + (1 << K));\n"
-      << "  (void)ST;\n"
+      << "  uint64_t *TQ = reinterpret_cast<uint64_t *>(ST + " << (P.max_stage > 0 ? P.max_stage : 1) << ");\n"
+      << "  (void)ST; (void)TQ;\n";
+    if (P.term_cache)
+        o << "  uint64_t *TCM = TQ + " << P.max_tot << ";\n"
+          << "  int64_t *TCQ = reinterpret_cast<int64_t *>(TCM + " << P.term_count << ");\n"
+          << "  cache_terms(kp, " << P.term_begin << ", " << P.term_count << ", TCM, TCQ, threadIdx.x, NT);\n";
+    o
       << "  __shared__ A TW[256];\n"
       << "  __shared__ uint64_t OUTT[4][256];\n"
       << "  __shared__ uint64_t CST[4];\n"
@@ -237,19 +248,43 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         o << "    { // round " << r << "\n";
         if (r == 0) o << "      cp_async_wait_all();\n";
         o << "      __syncthreads();\n";
-        const bool has_cst = (R.cst_count[0] | R.cst_count[1] | R.cst_count[2] | R.cst_count[3]) != 0;
-        if (R.term_count > 0 || has_cst) {
-            o << "      for (int j = tid; j < " << R.term_count << "; j += NT) {\n"
-              << "        const int g = " << R.term_begin << " + j;\n"
-              << "        const uint64_t q = (uint64_t)__ldg(kp.term_q + g);\n"
-              << "        StagedTerm t;\n"
-              << "        t.q = (__popcll(xo & __ldg(kp.term_mo + g)) & 1) ? (0ull - q) : q;\n"
-              << "        t.ml = __ldg(kp.term_ml + g);\n        t.pad = 0;\n        ST[j] = t;\n"
-              << "      }\n";
+        if (R.n_diag > 0) {
+            if (P.term_cache) {
+                // one thread per slot, spread over the warps; masks inline, angles from the cache
+                for (int j = 0; j < R.slot_count; j++) {
+                    const DevSlot &sl = S.slots[R.slot_begin + j];
+                    const int thr = ((j * 32) % NT + (j * 32) / NT) % NT;
+                    o << "      if (tid == " << thr << ") { uint64_t acc = 0ull;\n";
+                    for (int t = sl.tb; t < sl.tb + sl.tn; t++) {
+                        const int i = t - P.term_begin;
+                        o << "        { const uint64_t v = (uint64_t)TCQ[" << i << "]; acc += (__popcll(xo & "
+                          << hex64(S.term_mo[t]) << ") & 1) ? 0ull - v : v; }\n";
+                    }
+                    o << "        ST[" << j << "].q = acc; }\n";
+                }
+            } else {
+                o << "      stage_slots(xo, kp.slots, " << R.slot_begin << ", " << R.slot_count
+                  << ", kp.term_mo, kp.term_q, 0, ST, tid, NT);\n";
+            }
             for (int cc = 0; cc < 4; cc++)
                 if (R.cst_count[cc] > 0)
                     o << "      if (warp == " << (cc % (NT / 32)) << ") { const uint64_t v = warp_const_sum(xo, kp.cst_mo, kp.cst_q, "
                       << R.cst_begin[cc] << ", " << R.cst_count[cc] << ", lane); if (lane == 0) CST[" << cc << "] = v; }\n";
+            o << "      __syncthreads();\n";
+            // class totals, one thread each, spread over the warps
+            for (int k = 0; k < R.n_diag; k++) {
+                const DevDiag &d = S.diags[R.diag_begin + k];
+                for (int u = 0; u < 16; u++) {
+                    if (!diag_class_used(d, u)) continue;
+                    const int i = d.tot + u;
+                    const int thr = ((i * 32) % NT + (i * 32) / NT) % NT;
+                    o << "      if (tid == " << thr << ") TQ[" << i << "] = " << hex64(dbl_state ? 0 : (1ull << 31));
+                    if (d.zs[u] >= 0) o << " + ST[" << d.zs[u] << "].q";
+                    for (int j = d.off[u]; j < d.off[u + 1]; j++) o << " + ST[" << j << "].q";
+                    if (u == 0 && d.cst >= 0) o << " + CST[" << d.cst << "]";
+                    o << ";\n";
+                }
+            }
             o << "      __syncthreads();\n";
         }
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
@@ -291,28 +326,34 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                 const DevDiag &d = S.diags[op.arg];
                 const double sc = (op.pad && !table_scaled) ? P.scale : 1.0;
                 o << "      { uint64_t G[16];\n";
-                for (int s = 0; s < 16; s++) {
-                    const int b = d.off[s], e = d.off[s + 1];
-                    if (b == e) {
-                        o << "        G[" << s << "] = 0ull;\n";
+                const bool unrolled = d.off[16] <= 512;
+                for (int u = 0; u < 16; u++) {
+                    if (!diag_class_used(d, u)) {
+                        o << "        G[" << u << "] = 0ull;\n";
                         continue;
                     }
-                    o << "        { uint64_t acc0 = 0ull, acc1 = 0ull;\n"
-                      << "          #pragma unroll 4\n"
-                      << "          for (int j = " << b << "; j + 1 < " << e << "; j += 2) {\n"
-                      << "            const StagedTerm t0 = ST[j], t1 = ST[j + 1];\n"
-                      << "            acc0 += (__popc(lf & t0.ml) & 1) ? (0ull - t0.q) : t0.q;\n"
-                      << "            acc1 += (__popc(lf & t1.ml) & 1) ? (0ull - t1.q) : t1.q;\n"
-                      << "          }\n";
-                    if ((e - b) & 1)
-                        o << "          { const StagedTerm t0 = ST[" << e - 1 << "];\n"
-                          << "            acc0 += (__popc(lf & t0.ml) & 1) ? (0ull - t0.q) : t0.q; }\n";
-                    o << "          G[" << s << "] = acc0 + acc1; }\n";
+                    const int b = d.off[u], e = d.off[u + 1];
+                    o << "        { uint64_t o0 = 0ull, o1 = 0ull;\n";
+                    if (unrolled) {
+                        for (int j = b; j < e; j++) {
+                            const uint32_t ml = S.slots[R.slot_begin + j].ml;
+                            const char *acc = ((j - b) & 1) ? "o1" : "o0";
+                            if ((ml & (ml - 1)) == 0)
+                                o << "          if (lf & " << hex32(ml) << ") " << acc << " += ST[" << j << "].q;\n";
+                            else
+                                o << "          if (__popc(lf & " << hex32(ml) << ") & 1) " << acc << " += ST[" << j
+                                  << "].q;\n";
+                        }
+                    } else if (e > b) {
+                        o << "          #pragma unroll 4\n"
+                          << "          for (int j = " << b << "; j < " << e << "; j++) {\n"
+                          << "            const StagedTerm t0 = ST[j];\n"
+                          << "            if (__popc(lf & t0.ml) & 1) o0 += t0.q;\n"
+                          << "          }\n";
+                    }
+                    o << "          G[" << u << "] = TQ[" << d.tot + u << "] - 2ull * (o0 + o1); }\n";
                 }
-                if (d.cst >= 0) o << "        G[0] += CST[" << d.cst << "];\n";
-                o << "        wht16(G);\n"
-                  << "        #pragma unroll\n"
-                  << "        for (int s = 0; s < 16; s++) a[s] = rotate_tw(a[s], G[s], TW, (T)" << dbl(sc) << ");\n"
+                o << "        diag_rotate(a, G, TW, (T)" << dbl(sc) << ");\n"
                   << "      }\n";
             }
         }
@@ -499,8 +540,7 @@ std::string jit_build(const Schedule &S, int n, bool dbl_state, JitProgram &out)
         const std::string name = kernel_name(p, dbl_state);
         if (g_drv.get_function(&f, mods[p / chunk], name.c_str()) != CUDA_SUCCESS) return "missing kernel " + name;
         const size_t amp = dbl_state ? 16 : 8;
-        const size_t smem = 2 * (amp << S.K) + sizeof(StagedTerm) *
-                                                   (size_t)(S.passes[p].max_stage > 0 ? S.passes[p].max_stage : 1);
+        const size_t smem = pass_smem_bytes(S.passes[p], amp, S.K);
         if (g_drv.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
             return "cuFuncSetAttribute failed";
         int occ = 0;

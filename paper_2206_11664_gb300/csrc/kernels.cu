@@ -50,7 +50,8 @@ __device__ __forceinline__ void tile_pass_body(typename VT<T>::A *__restrict__ p
     extern __shared__ __align__(16) unsigned char smraw[];
     A *X = reinterpret_cast<A *>(smraw);                // exchange buffer (swizzled)
     A *Pf = X + (1 << K);                               // prefetch buffer (tile order)
-    StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf + (1 << K));
+    StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf + (1 << K));   // P.max_stage slots
+    uint64_t *TQ = nullptr;                             // P.max_tot class totals, after ST
     __shared__ DevPass P;
     __shared__ DevRound RR[kMaxRounds];
     __shared__ uint32_t swzc[16];
@@ -67,6 +68,18 @@ __device__ __forceinline__ void tile_pass_body(typename VT<T>::A *__restrict__ p
     if (tid == 0) P = kp.passes[pass_idx];
     __syncthreads();
     const int nr = P.n_rounds;
+    TQ = reinterpret_cast<uint64_t *>(ST + (P.max_stage > 0 ? P.max_stage : 1));
+    const uint64_t *tmo = kp.term_mo;
+    const int64_t *tqv = kp.term_q;
+    int toff = 0;
+    if (P.term_cache) {
+        uint64_t *TCM = TQ + P.max_tot;
+        int64_t *TCQ = reinterpret_cast<int64_t *>(TCM + P.term_count);
+        cache_terms(kp, P.term_begin, P.term_count, TCM, TCQ, tid, NT);
+        tmo = TCM;
+        tqv = TCQ;
+        toff = P.term_begin;
+    }
     if (tid < nr) RR[tid] = kp.rounds[P.round_begin + tid];
     if (tid < K) {
         uint32_t col = 1u << tid;
@@ -163,23 +176,16 @@ __device__ __forceinline__ void tile_pass_body(typename VT<T>::A *__restrict__ p
             const DevRound &R = RR[r];
             if (r == 0) cp_async_wait_all();
             __syncthreads();
-            const bool has_cst = (R.cst_count[0] | R.cst_count[1] | R.cst_count[2] | R.cst_count[3]) != 0;
-            if (R.term_count > 0 || has_cst) {
-                for (int j = tid; j < R.term_count; j += NT) {
-                    const int g = R.term_begin + j;
-                    const uint64_t q = (uint64_t)__ldg(kp.term_q + g);
-                    StagedTerm t;
-                    t.q = (__popcll(xo & __ldg(kp.term_mo + g)) & 1) ? (0 - q) : q;
-                    t.ml = __ldg(kp.term_ml + g);
-                    t.pad = 0;
-                    ST[j] = t;
-                }
+            if (R.n_diag > 0) {
+                stage_slots(xo, kp.slots, R.slot_begin, R.slot_count, tmo, tqv, toff, ST, tid, NT);
                 for (int c = warp; c < 4; c += NW)
                     if (R.cst_count[c] > 0) {
                         const uint64_t v = warp_const_sum(xo, kp.cst_mo, kp.cst_q, R.cst_begin[c],
                                                           R.cst_count[c], lane);
                         if (lane == 0) CST[c] = v;
                     }
+                __syncthreads();
+                stage_totals(kp, R.diag_begin, R.n_diag, ST, CST, TotalBias<A>::value, TQ, tid, NT);
                 __syncthreads();
             }
             const uint32_t v = LTL[r][lane] ^ LTW[r][warp];
@@ -318,8 +324,7 @@ __device__ __forceinline__ void tile_pass_body(typename VT<T>::A *__restrict__ p
                 default:
                     if ((code & 7) == D_DIAG) {
                         const DevDiag &dg = kp.diags[code >> 9];
-                        diag_apply(a, lf, dg, ST, TW, ((code >> 5) & 1) ? diag_scale : (T)1,
-                                   dg.cst >= 0 ? CST[dg.cst] : (uint64_t)0);
+                        diag_apply(a, lf, dg, ST, TQ, TW, ((code >> 5) & 1) ? diag_scale : (T)1);
                     }
                     break;
                 }
@@ -417,8 +422,8 @@ cudaError_t run_tile(void *psi, int n, const DevSchedule &S, int pass, int num_s
     using A = typename VT<T>::A;
     const int threads = 1 << (K - 4);
     const int d = sizeof(T) == 8;
-    const size_t smem = tile_smem_bytes<A, K>(S.host_passes[pass].max_stage);
-    const size_t smem_max = tile_smem_limit();
+    const size_t smem = pass_smem_bytes(S.host_passes[pass], sizeof(A), K);
+    const size_t smem_max = kTileSmemLimit;
     if (smem > smem_max) return cudaErrorInvalidConfiguration;
     if (!g_occ.init[d][K]) {
         cudaError_t e = cudaFuncSetAttribute(tile_pass_kernel<T, K>,
@@ -431,7 +436,7 @@ cudaError_t run_tile(void *psi, int n, const DevSchedule &S, int pass, int num_s
     if (e != cudaSuccess) return e;
     if (b < 1) b = 1;
     KParams kp{S.passes, S.rounds, S.ops, S.perms, S.diags, S.phases,
-               S.term_mo, S.term_ml, S.term_q, S.mask_pool, S.cst_mo, S.cst_q, S.c};
+               S.term_mo, S.slots, S.term_q, S.mask_pool, S.cst_mo, S.cst_q, S.c};
     int64_t ntiles = (int64_t)1 << (n - K);
     int64_t grid = (int64_t)num_sms * b;
     if (grid > ntiles) grid = ntiles;
@@ -778,7 +783,7 @@ cudaError_t run_batch(const BatchInstance *d_inst, const uint16_t *d_cta, int bl
     if (!init) {
         cudaError_t e = cudaFuncSetAttribute(tile_pass_batch_kernel<T, K>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tile_smem_limit());
+                                             (int)kTileSmemLimit);
         if (e != cudaSuccess) return e;
         init = true;
     }
@@ -824,11 +829,6 @@ cudaError_t launch_tile_pass_batch(bool dbl, int K, const BatchInstance *d_inst,
 #undef SD_BATCH_CASE
 }
 
-size_t tile_pass_smem(bool dbl, int K, int max_stage) {
-    const size_t amp = dbl ? 16 : 8;
-    return 2 * (amp << K) + 16 * (size_t)(max_stage > 0 ? max_stage : 1);
-}
-size_t tile_pass_smem_limit() { return tile_smem_limit(); }
 
 cudaError_t launch_tile_pass(bool dbl, void *psi, int n, const DevSchedule &S, int pass, int num_sms,
                              cudaStream_t st) {

@@ -19,7 +19,7 @@ struct DevSchedule {
     DevDiag *diags = nullptr;
     DevPhase *phases = nullptr;
     uint64_t *term_mo = nullptr;
-    uint32_t *term_ml = nullptr;
+    DevSlot *slots = nullptr;
     int64_t *term_q = nullptr;
     uint64_t *mask_pool = nullptr;
     uint64_t *cst_mo = nullptr;
@@ -65,8 +65,6 @@ cudaError_t launch_tile_pass_batch(bool dbl, int K, const BatchInstance *d_inst,
 int tile_pass_batch_occupancy(bool dbl, int K, size_t smem);
 
 // Dynamic shared memory of a tile pass and its limit.
-size_t tile_pass_smem(bool dbl, int K, int max_stage);
-size_t tile_pass_smem_limit();
 
 cudaError_t launch_tile_pass(bool dbl, void *psi, int n, const DevSchedule &S, int pass,
                              int num_sms, cudaStream_t st);

@@ -406,6 +406,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
 
         DevPass P{};
         P.round_begin = (int)S.rounds.size();
+        P.term_begin = (int)S.term_q.size();
         const int pass_op_begin = (int)S.ops.size();
         for (int p = 0; p < K; p++) P.tile_bits[p] = (uint8_t)tq[p];
         int no = 0;
@@ -466,7 +467,9 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             R.perm = -1;
             R.flags = is_load ? 1 : 0;
             R.op_begin = (int)S.ops.size();
-            R.term_begin = (int)S.term_q.size();
+            R.slot_begin = (int)S.slots.size();
+            R.diag_begin = (int)S.diags.size();
+            R.n_diag = 0;
             // -------- execute what is ready
             std::vector<Gate> perm_cnots;
             int executed = 0;
@@ -564,7 +567,6 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                         }
                         DevDiag dd{};
                         dd.cst = -1;
-                        int off = (int)S.term_q.size() - R.term_begin;
                         uint64_t outer_mask = 0, tile_mask = 0;
                         for (int k = 0; k < no; k++) outer_mask |= uint64_t(1) << P.outer_bits[k];
                         for (int p = 0; p < K; p++) tile_mask |= uint64_t(1) << tq[p];
@@ -581,21 +583,53 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                             R.cst_count[slot] = (int)S.cst_q.size() - R.cst_begin[slot];
                             if (R.cst_count[slot] > 0) dd.cst = slot;
                         }
+                        if (R.n_diag == 0) R.diag_begin = (int)S.diags.size();
+                        dd.tot = 16 * R.n_diag++;
+                        // per class, the terms grouped by their mask on the fixed positions
+                        std::vector<std::vector<std::pair<uint32_t, int>>> byc(16);
                         for (int s = 0; s < 16; s++) {
-                            dd.off[s] = off;
                             for (int t : cls[s]) {
                                 if (dd.cst >= 0 && s == 0 && !(D.masks[t] & tile_mask)) continue;
                                 uint32_t ml = 0;
                                 for (int p = 0; p < K; p++)
                                     if (!((regmask >> tq[p]) & 1) && ((D.masks[t] >> tq[p]) & 1))
                                         ml |= 1u << p;
+                                byc[s].push_back({ml, t});
+                            }
+                            std::stable_sort(byc[s].begin(), byc[s].end(),
+                                             [](const std::pair<uint32_t, int> &a,
+                                                const std::pair<uint32_t, int> &b) { return a.first < b.first; });
+                        }
+                        auto emit = [&](int s, size_t i0, size_t i1) {
+                            DevSlot sl{(int32_t)S.term_q.size(), (int32_t)(i1 - i0), byc[s][i0].first, 0};
+                            for (size_t i = i0; i < i1; i++) {
+                                const int t = byc[s][i].second;
                                 S.term_mo.push_back(D.masks[t] & outer_mask);
-                                S.term_ml.push_back(ml);
                                 S.term_q.push_back(D.q[t]);
-                                off++;
+                            }
+                            S.slots.push_back(sl);
+                        };
+                        for (int s = 0; s < 16; s++) {       // slots with a fixed-position mask
+                            dd.off[s] = (int)S.slots.size() - R.slot_begin;
+                            size_t i = 0;
+                            while (i < byc[s].size() && byc[s][i].first == 0) i++;
+                            while (i < byc[s].size()) {
+                                size_t e = i;
+                                while (e < byc[s].size() && byc[s][e].first == byc[s][i].first) e++;
+                                emit(s, i, e);
+                                i = e;
                             }
                         }
-                        dd.off[16] = off;
+                        dd.off[16] = (int)S.slots.size() - R.slot_begin;
+                        for (int s = 0; s < 16; s++) {       // slots constant over the thread's fixed positions
+                            dd.zs[s] = -1;
+                            size_t e = 0;
+                            while (e < byc[s].size() && byc[s][e].first == 0) e++;
+                            if (e > 0) {
+                                dd.zs[s] = (int)S.slots.size() - R.slot_begin;
+                                emit(s, 0, e);
+                            }
+                        }
                         S.diags.push_back(dd);
                         S.ops.push_back(DevOp{D_DIAG, 0, (int32_t)S.diags.size() - 1, 0});
                         if (diag_op_index < 0) diag_op_index = (int)S.ops.size() - 1;
@@ -607,7 +641,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             }
             while (first < N && done[first] >= 0) first++;
             R.op_end = (int)S.ops.size();
-            R.term_count = (int)S.term_q.size() - R.term_begin;
+            R.slot_count = (int)S.slots.size() - R.slot_begin;
             if (!perm_cnots.empty()) {
                 DevPerm pm{};
                 for (int p = 0; p < K; p++) {
@@ -644,8 +678,10 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             for (int i = 0; i < 4; i++) R.reg_pos[i] = (uint8_t)(c + i);
             R.perm = -1;
             R.op_begin = R.op_end = (int)S.ops.size();
-            R.term_begin = (int)S.term_q.size();
-            R.term_count = 0;
+            R.slot_begin = (int)S.slots.size();
+            R.slot_count = 0;
+            R.diag_begin = (int)S.diags.size();
+            R.n_diag = 0;
             R.flags = 0;
             S.rounds.push_back(R);
             nr++;
@@ -656,13 +692,22 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             assign_layout(S.rounds[r], K, c, (S.rounds[r].flags & 3) != 0);
         P.n_rounds = (int)S.rounds.size() - P.round_begin;
         P.max_stage = 0;
-        for (int r = P.round_begin; r < (int)S.rounds.size(); r++)
-            P.max_stage = std::max(P.max_stage, S.rounds[r].term_count);
+        P.max_tot = 0;
+        for (int r = P.round_begin; r < (int)S.rounds.size(); r++) {
+            P.max_stage = std::max(P.max_stage, S.rounds[r].slot_count);
+            P.max_tot = std::max(P.max_tot, 16 * S.rounds[r].n_diag);
+        }
         P.scale = std::ldexp(1.0, -(h_count / 2)) * ((h_count & 1) ? std::sqrt(0.5) : 1.0);
         if (diag_op_index >= 0) {
             P.scale_in_diag = 1;
             S.ops[diag_op_index].pad = 1;
             S.diag_passes++;
+        }
+        P.term_count = (int)S.term_q.size() - P.term_begin;
+        P.term_cache = 0;
+        if (P.term_count > 0 && P.term_count <= kTermCache) {
+            P.term_cache = 1;
+            if (pass_smem_bytes(P, size_t(128) >> c, K) > kTileSmemLimit) P.term_cache = 0;
         }
         S.passes.push_back(P);
     }

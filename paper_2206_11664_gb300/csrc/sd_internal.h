@@ -125,7 +125,7 @@ struct Schedule {
     std::vector<DevDiag> diags;
     std::vector<DevPhase> phases;
     std::vector<uint64_t> term_mo;      // diag term pool: mask on the outer qubits
-    std::vector<uint32_t> term_ml;      // diag term pool: mask on the round's fixed tile positions
+    std::vector<DevSlot> slots;         // diag term slots (class, mask on the round's fixed positions)
     std::vector<int64_t> term_q;        // diag term pool: Q0.64 turns
     std::vector<uint64_t> cst_mo;       // tile-constant terms: outer mask
     std::vector<int64_t> cst_q;         // tile-constant terms: Q0.64 turns

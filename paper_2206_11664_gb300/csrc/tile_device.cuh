@@ -108,6 +108,17 @@ __device__ __forceinline__ void wht16(uint64_t *G) {
                 G[s | (1 << i)] = u - v;
             }
 }
+__device__ __forceinline__ void wht16(uint32_t *G) {
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int s = 0; s < 16; s++)
+            if (!((s >> i) & 1)) {
+                uint32_t u = G[s], v = G[s | (1 << i)];
+                G[s] = u + v;
+                G[s | (1 << i)] = u - v;
+            }
+}
 __device__ __forceinline__ void wht16(double *G) {
 #pragma unroll
     for (int i = 0; i < 4; i++)
@@ -138,6 +149,21 @@ __device__ __forceinline__ float2 rotate_tw(float2 a, uint64_t t, const float2 *
     o.y = a.y * C - a.x * S;
     return o;
 }
+// The same rotation for Q0.32 turns (single precision): the top 8 bits index
+// the table, the low 24 bits are the remaining angle, exact in a float.
+__device__ __forceinline__ float2 rotate_tw32(float2 a, uint32_t t, const float2 *__restrict__ tw, float sc) {
+    const float2 e = tw[t >> 24];
+    const float phi = (float)(t & 0xffffffu) * (float)(6.283185307179586 / 4294967296.0);
+    const float p2 = phi * phi;
+    const float cp = fmaf(p2, fmaf(p2, 1.0f / 24.0f, -0.5f), 1.0f);
+    const float sp = phi * fmaf(p2, -1.0f / 6.0f, 1.0f);
+    const float C = (e.x * cp - e.y * sp) * sc;
+    const float S = (e.y * cp + e.x * sp) * sc;
+    float2 o;
+    o.x = a.x * C + a.y * S;
+    o.y = a.y * C - a.x * S;
+    return o;
+}
 __device__ __forceinline__ double2 rotate_tw(double2 a, uint64_t t, const double2 *__restrict__ tw, double sc) {
     const double2 e = tw[t >> 56];
     const uint64_t r = (t << 8) >> 12;             // 52 bits below the table index
@@ -155,36 +181,104 @@ __device__ __forceinline__ double2 rotate_tw(double2 a, uint64_t t, const double
 
 
 
-// Group exponential on the thread's 16 amplitudes: T(s) = sum_j q_j
-// (-1)^{|x & m_j|} with x = (tile, fixed positions lf, register bits s).
-// Terms are sorted by their register projection u (class u); per class the
-// sum over the fixed positions gives G[u], and a 4-level Walsh-Hadamard
-// transform over the register bits turns G into T.
+// Rounding bias of the class totals: complex64 passes finish the angle in
+// Q0.32 (the high word of G + 2^31 is G rounded to 2^-32 turns, the float
+// rotation's own resolution); complex128 passes keep Q0.64.
+template <typename A> struct TotalBias;
+template <> struct TotalBias<float2> { static constexpr uint64_t value = 1ull << 31; };
+template <> struct TotalBias<double2> { static constexpr uint64_t value = 0ull; };
+
+// Angles T from the class sums G by the 4-level Walsh-Hadamard transform over
+// the register bits, then the rotation of the thread's 16 amplitudes.
+__device__ __forceinline__ void diag_rotate(float2 *a, const uint64_t *G, const float2 *__restrict__ tw,
+                                            float sc) {
+    uint32_t g[16];
+#pragma unroll
+    for (int s = 0; s < 16; s++) g[s] = (uint32_t)(G[s] >> 32);
+    wht16(g);
+#pragma unroll
+    for (int s = 0; s < 16; s++) a[s] = rotate_tw32(a[s], g[s], tw, sc);
+}
+__device__ __forceinline__ void diag_rotate(double2 *a, uint64_t *G, const double2 *__restrict__ tw,
+                                            double sc) {
+    wht16(G);
+#pragma unroll
+    for (int s = 0; s < 16; s++) a[s] = rotate_tw(a[s], G[s], tw, sc);
+}
+
+// Group exponential on the thread's 16 amplitudes (layout of DevDiag): per
+// class u, G[u] = TQ[tot + u] - 2 (sum of the slots with odd |lf & ml|).
 template <typename A, typename T>
 __device__ __forceinline__ void diag_apply(A *a, uint32_t lf, const DevDiag &d,
                                            const StagedTerm *__restrict__ st,
-                                           const A *__restrict__ tw, T sc, uint64_t g0) {
+                                           const uint64_t *__restrict__ TQ,
+                                           const A *__restrict__ tw, T sc) {
     uint64_t G[16];
 #pragma unroll
     for (int s = 0; s < 16; s++) {
-        uint64_t acc0 = 0, acc1 = 0;
+        uint64_t o0 = 0, o1 = 0;
         int j = d.off[s];
         const int e = d.off[s + 1];
         for (; j + 1 < e; j += 2) {
             const StagedTerm t0 = st[j], t1 = st[j + 1];
-            acc0 += (__popc(lf & t0.ml) & 1) ? (0 - t0.q) : t0.q;
-            acc1 += (__popc(lf & t1.ml) & 1) ? (0 - t1.q) : t1.q;
+            if (__popc(lf & t0.ml) & 1) o0 += t0.q;
+            if (__popc(lf & t1.ml) & 1) o1 += t1.q;
         }
         if (j < e) {
             const StagedTerm t0 = st[j];
-            acc0 += (__popc(lf & t0.ml) & 1) ? (0 - t0.q) : t0.q;
+            if (__popc(lf & t0.ml) & 1) o0 += t0.q;
         }
-        G[s] = acc0 + acc1;
+        G[s] = TQ[d.tot + s] - 2ull * (o0 + o1);
     }
-    G[0] += g0;
-    wht16(G);
-#pragma unroll
-    for (int s = 0; s < 16; s++) a[s] = rotate_tw(a[s], G[s], tw, sc);
+    diag_rotate(a, G, tw, sc);
+}
+
+// Term slots of a round staged for the tile with outer bits xo: ST[j] holds
+// the slot's signed angle sum sum_t q_t (-1)^{|xo & mo_t|} and its mask ml.
+// Term t is read at mo[t - toff], q[t - toff] (the pass's cached copy in
+// shared memory, or the global arrays with toff = 0).
+__device__ __forceinline__ void stage_slots(uint64_t xo, const DevSlot *__restrict__ slots, int slot_begin,
+                                            int slot_count, const uint64_t *mo, const int64_t *q, int toff,
+                                            StagedTerm *ST, int tid, int nt) {
+    for (int j = tid; j < slot_count; j += nt) {
+        const DevSlot sl = slots[slot_begin + j];
+        uint64_t acc = 0;
+        for (int t = sl.tb - toff; t < sl.tb - toff + sl.tn; t++) {
+            const uint64_t v = (uint64_t)q[t];
+            acc += (__popcll(xo & mo[t]) & 1) ? (0 - v) : v;
+        }
+        StagedTerm st;
+        st.q = acc;
+        st.ml = sl.ml;
+        st.pad = 0;
+        ST[j] = st;
+    }
+}
+
+// Copy of the pass's terms into shared memory (TCM: outer masks, TCQ: angles).
+__device__ __forceinline__ void cache_terms(const KParams &kp, int term_begin, int term_count, uint64_t *TCM,
+                                            int64_t *TCQ, int tid, int nt) {
+    for (int i = tid; i < term_count; i += nt) {
+        TCM[i] = __ldg(kp.term_mo + term_begin + i);
+        TCQ[i] = __ldg(kp.term_q + term_begin + i);
+    }
+}
+
+// Class totals of the round's group exponentials (after stage_slots and the
+// tile-constant sums CST): TQ[16 k + u] = bias + sum of class u's slots of
+// the k-th exponential, plus its tile constant in class 0.
+__device__ __forceinline__ void stage_totals(const KParams &kp, int diag_begin, int n_diag,
+                                             const StagedTerm *ST, const uint64_t *CST, uint64_t bias,
+                                             uint64_t *TQ, int tid, int nt) {
+    for (int i = tid; i < 16 * n_diag; i += nt) {
+        const DevDiag &d = kp.diags[diag_begin + (i >> 4)];
+        const int u = i & 15;
+        uint64_t t = bias;
+        if (d.zs[u] >= 0) t += ST[d.zs[u]].q;
+        for (int j = d.off[u]; j < d.off[u + 1]; j++) t += ST[j].q;
+        if (u == 0 && d.cst >= 0) t += CST[d.cst];
+        TQ[i] = t;
+    }
 }
 
 // S/CZ layer: a(x) *= i^{k(x)}, k = |x&sp| - |x&sm| + 2 sum_CZ x_c x_t.
@@ -242,16 +336,5 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Dynamic shared memory available to a tile pass (227 KB per block minus the
-// static tables of the kernel).
-__host__ __device__ constexpr size_t tile_smem_limit() { return 227 * 1024 - 28 * 1024; }
-
-// Shared-memory size of a tile pass: exchange + prefetch buffers, staged terms.
-template <typename A, int K>
-__host__ __device__ constexpr size_t tile_smem_bytes(int max_stage) {
-    return 2 * (sizeof(A) << K) + sizeof(StagedTerm) * (size_t)(max_stage > 0 ? max_stage : 1);
-}
-
 
 }  // namespace sd

@@ -124,6 +124,8 @@ def test_tile_heisenberg_lattice(sd, dtype):
     psi0 = basis_state(16, neel_index(4, 4))
     for rule in (0, 1, 2):
         _check(sd, h, psi0, 0.02, 10, 1, dtype, skip_rule=rule)
+    # second order over 6 steps: head, one block of 4 merged cores, one core, tail
+    _check(sd, h, psi0, 0.02, 6, 2, dtype)
 
 
 def test_tile_jw_like(sd):
@@ -280,7 +282,8 @@ def test_full_size_heisenberg_n30(sd, dtype):
     h = heisenberg_lattice(5, 6)
     cdt = torch.complex64 if dtype == "c64" else torch.complex128
     sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
-    steps = 2
+    steps = 5   # one block of 4 merged steps and a single step, as in the benchmark's calls
+    sim.prepare(sd.C64 if dtype == "c64" else sd.C128, 0.02, steps, 1)
     a = torch.zeros(1 << 30, dtype=cdt, device="cuda")
     a[neel_index(5, 6)] = 1
     b = a.clone()

@@ -134,3 +134,25 @@ def test_schedule_stats_small_state_is_onchip(sd):
     t = tfim_chain(10)
     sim = sd.Simulator(t.n, t.x, t.z, t.c).plan()
     assert sim.schedule_stats(sd.C128, 1)["onchip"]
+
+
+def test_count_passes_blocks(sd):
+    """Launch counts of sd_evolve: one step is one schedule; longer calls
+    merge 4 steps (first order) or 4 cores (second order) into one schedule,
+    which needs fewer passes than 4 separate ones; the on-chip path has none."""
+    h = heisenberg_lattice(5, 6)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    one = sim.schedule_stats(sd.C64, 1)["passes_per_step"]
+    assert sim.count_passes(sd.C64, 1, 0) == 0
+    assert sim.count_passes(sd.C64, 1, 1) == one
+    four = sim.count_passes(sd.C64, 1, 4)
+    assert four < 4 * one
+    assert sim.count_passes(sd.C64, 1, 8) == 2 * four
+    assert sim.count_passes(sd.C64, 1, 9) == 2 * four + one
+    c2 = sim.count_passes(sd.C64, 2, 6)
+    assert 0 < c2 < 6 * sim.schedule_stats(sd.C64, 2)["passes_per_step"] + 10
+    t = tfim_chain(10)
+    small = sd.Simulator(t.n, t.x, t.z, t.c).plan()
+    assert small.count_passes(sd.C128, 1, 100) == 0
+    with pytest.raises(sd.SDError):
+        sim.count_passes(sd.C64, 3, 1)
