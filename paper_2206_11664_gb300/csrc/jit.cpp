@@ -25,6 +25,7 @@
 #include <atomic>
 #include <thread>
 #include <algorithm>
+#include <cmath>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -158,6 +159,40 @@ std::string kernel_name(int pi, bool dbl_state) {
     return std::string(dbl_state ? "sd_pass_c128_" : "sd_pass_c64_") + std::to_string(pi);
 }
 
+// Fixed-point one-qubit Cliffords on register slot I.  Register s holds its
+// amplitude times i^-kph[s] (kph fixed at generation time, since the slot
+// bits are): the output phase i^B of S^B H S^PA stays in kph, and i^m for the
+// operands' phase difference m only chooses adds or subtracts of the parts.
+void emit_had_fx(std::ostringstream &o, int I, int PA, int B, int *kph) {
+    static const char *form[4] = {
+        "ar[%d] = ur + vr; ai[%d] = ui + vi; ar[%d] = ur - vr; ai[%d] = ui - vi;",
+        "ar[%d] = ur - vi; ai[%d] = ui + vr; ar[%d] = ur + vi; ai[%d] = ui - vr;",
+        "ar[%d] = ur - vr; ai[%d] = ui - vi; ar[%d] = ur + vr; ai[%d] = ui + vi;",
+        "ar[%d] = ur + vi; ai[%d] = ui - vr; ar[%d] = ur - vi; ai[%d] = ui + vr;"};
+    for (int s = 0; s < 16; s++) {
+        if ((s >> I) & 1) continue;
+        const int t = s | (1 << I);
+        const int m = (PA + kph[t] - kph[s]) & 3;
+        char buf[256];
+        snprintf(buf, sizeof buf, form[m], s, s, t, t);
+        o << "      { const long long ur = ar[" << s << "], ui = ai[" << s << "], vr = ar[" << t << "], vi = ai[" << t
+          << "]; " << buf << " }\n";
+        kph[t] = (B + kph[s]) & 3;
+    }
+}
+void emit_mono_fx(std::ostringstream &o, int I, int PA, int XX, int *kph) {
+    for (int s = 0; s < 16; s++) {
+        if ((s >> I) & 1) continue;
+        const int t = s | (1 << I);
+        kph[t] = (kph[t] + PA) & 3;
+        if (XX) {
+            o << "      { const long long r = ar[" << s << "], i = ai[" << s << "]; ar[" << s << "] = ar[" << t
+              << "]; ai[" << s << "] = ai[" << t << "]; ar[" << t << "] = r; ai[" << t << "] = i; }\n";
+            std::swap(kph[s], kph[t]);
+        }
+    }
+}
+
 // Whether class u of a group exponential has any term on the tile.
 bool diag_class_used(const DevDiag &d, int u) {
     return d.off[u + 1] > d.off[u] || d.zs[u] >= 0 || (u == 0 && d.cst >= 0);
@@ -182,6 +217,28 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     }
     const bool table_scaled = P.scale_in_diag && n_diag == 1;
     const double table_scale = table_scaled ? P.scale : 1.0;
+    // Complex128 passes run in fixed point (fx): each round ends with an
+    // arithmetic shift that applies the 1/2 of each pair of its Hadamards
+    // (a lone 1/sqrt(2) is carried to the next round); one left at the end of
+    // the pass goes into the rotation table of its only group exponential,
+    // or (none or several of them) into a multiply before the
+    // store.  Headroom fx_hr: a tile's norm is invariant in a pass, so a
+    // component never exceeds 2^((K+1)/2) times the tile's largest one, and a
+    // round's unnormalised butterflies add at most (h+1)/2 bits before its shift.
+    const bool fx = dbl_state;
+    std::vector<int> fx_shift(P.n_rounds, 0);
+    int fx_hmax = 0, fx_pend = 0;
+    for (int r = 0; r < P.n_rounds; r++) {
+        const DevRound &R = S.rounds[P.round_begin + r];
+        int h = 0;
+        for (int oi = R.op_begin; oi < R.op_end; oi++) h += S.ops[oi].kind == D_HAD;
+        fx_hmax = std::max(fx_hmax, h);
+        fx_shift[r] = (fx_pend + h) >> 1;
+        fx_pend = (fx_pend + h) & 1;
+    }
+    const int fx_hr = (K + 2) / 2 + 2 + (fx_hmax + 2) / 2;
+    const bool fx_res_table = fx && fx_pend && n_diag == 1;
+    const bool fx_res_store = fx && fx_pend && n_diag != 1;
     std::ostringstream o;
     o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << kernel_name(pi, dbl_state)
       << "(A *__restrict__ psi, sd::KParams kp) {\n"
@@ -197,16 +254,30 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         o << "  uint64_t *TCM = TQ + " << P.max_tot << ";\n"
           << "  int64_t *TCQ = reinterpret_cast<int64_t *>(TCM + " << P.term_count << ");\n"
           << "  cache_terms(kp, " << P.term_begin << ", " << P.term_count << ", TCM, TCQ, threadIdx.x, NT);\n";
+    if (fx)
+        o << "  longlong2 *XI = reinterpret_cast<longlong2 *>(X);\n"
+          << "  __shared__ longlong2 T1[256], T2[256];\n"
+          << "  __shared__ uint32_t EM[NT / 32];\n";
+    else
+        o << "  __shared__ A TW[256];\n";
     o
-      << "  __shared__ A TW[256];\n"
       << "  __shared__ uint64_t OUTT[4][256];\n"
       << "  __shared__ uint64_t CST[4];\n"
       << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n"
       << "  (void)lane; (void)warp;\n"
       << "  for (int i = tid; i < 256; i += NT) {\n"
-      << "    double sn, cs;\n    sincospi((double)i / 128.0, &sn, &cs);\n"
-      << "    TW[i].x = (T)(cs * " << dbl(table_scale) << ");\n    TW[i].y = (T)(sn * " << dbl(table_scale)
-      << ");\n";
+      << "    double sn, cs;\n    sincospi((double)i / 128.0, &sn, &cs);\n";
+    if (fx) {
+        const double q62 = 4611686018427387904.0, t1s = fx_res_table ? q62 * std::sqrt(0.5) : q62;
+        o << "    T1[i] = make_longlong2(__double2ll_rn(cs * " << dbl(t1s) << "), __double2ll_rn(sn * " << dbl(t1s)
+          << "));\n"
+          << "    sincospi((double)i / 32768.0, &sn, &cs);\n"
+          << "    T2[i] = make_longlong2(__double2ll_rn(cs * " << dbl(q62) << "), __double2ll_rn(sn * " << dbl(q62)
+          << "));\n";
+    } else {
+        o << "    TW[i].x = (T)(cs * " << dbl(table_scale) << ");\n    TW[i].y = (T)(sn * " << dbl(table_scale)
+          << ");\n";
+    }
     for (int byte = 0; byte < 4; byte++) {
         o << "    OUTT[" << byte << "][i] = 0ull";
         for (int b = 0; b < 8; b++) {
@@ -241,8 +312,9 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     o << ";\n  };\n  (void)swz;\n";
     o << "  long long tile = blockIdx.x;\n  if (tile < ntiles) prefetch(tile);\n"
       << "  for (; tile < ntiles; tile += gridDim.x) {\n"
-      << "    const uint64_t xo = deposit(tile);\n"
-      << "    A a[16];\n";
+      << "    const uint64_t xo = deposit(tile);\n";
+    if (fx) o << "    long long ar[16], ai[16];\n    uint32_t Sx = 0u;\n";
+    else o << "    A a[16];\n";
     for (int r = 0; r < P.n_rounds; r++) {
         const DevRound &R = S.rounds[P.round_begin + r];
         o << "    { // round " << r << "\n";
@@ -290,7 +362,28 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t sw = " << thread_expr(R, K, swc, false) << ";\n"
           << "      (void)lf; (void)sw;\n";
-        if (r == 0) {
+        if (r == 0 && fx) {
+            // the tile's largest exponent, then the fixed-point conversion
+            o << "      { double2 d[16];\n        uint32_t em = 0u;\n";
+            for (int s = 0; s < 16; s++) {
+                uint32_t l = 0;
+                for (int i = 0; i < 4; i++)
+                    if ((s >> i) & 1) l |= 1u << R.reg_pos[i];
+                o << "        d[" << s << "] = Pf[lf | " << hex32(l) << "];\n"
+                  << "        em = max(em, max(fx_exp(d[" << s << "].x), fx_exp(d[" << s << "].y)));\n";
+            }
+            o << "        em = __reduce_max_sync(0xffffffffu, em);\n"
+              << "        if (lane == 0) EM[warp] = em;\n"
+              << "        __syncthreads();\n"
+              << "        Sx = EM[0];\n"
+              << "        #pragma unroll\n"
+              << "        for (int w = 1; w < NT / 32; w++) Sx = max(Sx, EM[w]);\n"
+              << "        #pragma unroll\n"
+              << "        for (int s = 0; s < 16; s++) { ar[s] = fx_from(d[s].x, Sx, " << fx_hr
+              << "); ai[s] = fx_from(d[s].y, Sx, " << fx_hr << "); }\n"
+              << "      }\n"
+              << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);\n";
+        } else if (r == 0) {
             for (int s = 0; s < 16; s++) {
                 uint32_t l = 0;
                 for (int i = 0; i < 4; i++)
@@ -304,16 +397,25 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                 uint32_t cs = 0;
                 for (int i = 0; i < 4; i++)
                     if ((s >> i) & 1) cs ^= (uint32_t)swc(R.reg_pos[i]);
-                o << "      a[" << s << "] = X[sw ^ " << hex32(cs) << "];\n";
+                if (fx)
+                    o << "      { const longlong2 v = XI[sw ^ " << hex32(cs) << "]; ar[" << s << "] = v.x; ai[" << s
+                      << "] = v.y; }\n";
+                else
+                    o << "      a[" << s << "] = X[sw ^ " << hex32(cs) << "];\n";
             }
         }
+        int kph[16] = {0};   // fx: register s holds i^-kph[s] times its amplitude
         bool need_xf = (R.flags & 2) != 0;
         for (int oi = R.op_begin; oi < R.op_end; oi++)
             need_xf |= S.ops[oi].kind == D_PHASE;
         if (need_xf) o << "      const uint64_t xf = xo | " << thread_expr(R, K, gbit, true) << ";\n";
         for (int oi = R.op_begin; oi < R.op_end; oi++) {
             const DevOp &op = S.ops[oi];
-            if (op.kind == D_HAD) {
+            if (op.kind == D_HAD && fx) {
+                emit_had_fx(o, op.slot, c1_a(op.arg), c1_b(op.arg), kph);
+            } else if (op.kind == D_MONO && fx) {
+                emit_mono_fx(o, op.slot, c1_a(op.arg), c1_x(op.arg), kph);
+            } else if (op.kind == D_HAD) {
                 o << "      had_fixed<" << op.slot << ", " << c1_a(op.arg) << ", " << c1_b(op.arg) << ">(a);\n";
             } else if (op.kind == D_MONO) {
                 o << "      mono_fixed<" << op.slot << ", " << c1_a(op.arg) << ", " << c1_x(op.arg) << ">(a);\n";
@@ -321,7 +423,8 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                 o << "      { const int gq[4] = {" << (int)P.tile_bits[R.reg_pos[0]] << ", "
                   << (int)P.tile_bits[R.reg_pos[1]] << ", " << (int)P.tile_bits[R.reg_pos[2]] << ", "
                   << (int)P.tile_bits[R.reg_pos[3]] << "};\n"
-                  << "        phase_apply(a, xf, gq, kp.phases[" << op.arg << "], kp.mask_pool); }\n";
+                  << (fx ? "        fx_phase_apply(ar, ai, xf, gq, kp.phases[" : "        phase_apply(a, xf, gq, kp.phases[")
+                  << op.arg << "], kp.mask_pool); }\n";
             } else {
                 const DevDiag &d = S.diags[op.arg];
                 const double sc = (op.pad && !table_scaled) ? P.scale : 1.0;
@@ -353,11 +456,39 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                     }
                     o << "          G[" << u << "] = TQ[" << d.tot + u << "] - 2ull * (o0 + o1); }\n";
                 }
-                o << "        diag_rotate(a, G, TW, (T)" << dbl(sc) << ");\n"
-                  << "      }\n";
+                if (fx)
+                    o << "        wht16(G);\n"
+                      << "        #pragma unroll\n"
+                      << "        for (int s = 0; s < 16; s++) fx_rotate(ar[s], ai[s], G[s], T1, T2);\n"
+                      << "      }\n";
+                else
+                    o << "        diag_rotate(a, G, TW, (T)" << dbl(sc) << ");\n"
+                      << "      }\n";
             }
         }
-        if (R.flags & 2) {
+        if (fx) {
+            const int sh = fx_shift[r];
+            if (sh > 0)
+                o << "      #pragma unroll\n"
+                  << "      for (int s = 0; s < 16; s++) { ar[s] = (ar[s] + " << (1ll << (sh - 1)) << "ll) >> " << sh
+                  << "; ai[s] = (ai[s] + " << (1ll << (sh - 1)) << "ll) >> " << sh << "; }\n";
+            for (int s2 = 0; s2 < 16; s2++)
+                if (kph[s2]) o << "      fx_mul_ipow(ar[" << s2 << "], ai[" << s2 << "], " << kph[s2] << ");\n";
+        }
+        if ((R.flags & 2) && fx) {
+            if (fx_res_store)
+                o << "      #pragma unroll\n"
+                  << "      for (int s = 0; s < 16; s++) { ar[s] = __mul64hi(ar[s], kRsqrt2Q63); ai[s] = __mul64hi(ai[s], kRsqrt2Q63); }\n";
+            o << "      { const int U = (int)Sx - " << (1085 - fx_hr - (fx_res_store ? 1 : 0)) << ";\n";
+            for (int s = 0; s < 16; s++) {
+                uint64_t g = 0;
+                for (int i = 0; i < 4; i++)
+                    if ((s >> i) & 1) g |= gbit(R.reg_pos[i]);
+                o << "        psi[xf | " << hex64(g) << "] = make_double2(fx_to(ar[" << s << "], U), fx_to(ai[" << s
+                  << "], U));\n";
+            }
+            o << "      }\n";
+        } else if (R.flags & 2) {
             for (int s = 0; s < 16; s++) {
                 uint64_t g = 0;
                 for (int i = 0; i < 4; i++)
@@ -380,15 +511,21 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
               << (int)R.reg_pos[1] << "]), c2 = swz(pm.col[" << (int)R.reg_pos[2] << "]), c3 = swz(pm.col["
               << (int)R.reg_pos[3] << "]);\n"
               << "        #pragma unroll\n"
-              << "        for (int s = 0; s < 16; s++) X[base ^ ((s & 1) ? c0 : 0u) ^ ((s & 2) ? c1 : 0u) ^ "
-                 "((s & 4) ? c2 : 0u) ^ ((s & 8) ? c3 : 0u)] = a[s];\n"
+              << "        for (int s = 0; s < 16; s++) "
+              << (fx ? "XI" : "X")
+              << "[base ^ ((s & 1) ? c0 : 0u) ^ ((s & 2) ? c1 : 0u) ^ "
+                 "((s & 4) ? c2 : 0u) ^ ((s & 8) ? c3 : 0u)] = "
+              << (fx ? "make_longlong2(ar[s], ai[s])" : "a[s]") << ";\n"
               << "      }\n";
         } else {
             for (int s = 0; s < 16; s++) {
                 uint32_t cs = 0;
                 for (int i = 0; i < 4; i++)
                     if ((s >> i) & 1) cs ^= (uint32_t)swc(R.reg_pos[i]);
-                o << "      X[sw ^ " << hex32(cs) << "] = a[" << s << "];\n";
+                if (fx)
+                    o << "      XI[sw ^ " << hex32(cs) << "] = make_longlong2(ar[" << s << "], ai[" << s << "]);\n";
+                else
+                    o << "      X[sw ^ " << hex32(cs) << "] = a[" << s << "];\n";
             }
         }
         o << "    }\n";

@@ -260,6 +260,31 @@ def test_jit_heisenberg_and_random(sd, dtype):
     _check(sd, h2, _rand_state(rng, 15), 0.05, 2, 1, dtype, tile_bits=11, jit=1)
 
 
+def test_jit_complex128_fixed_point(sd):
+    """Complex128 passes compiled at run time compute in 64-bit fixed point
+    with one binary exponent per tile: CNOT permutations, S/CZ layers, many
+    groups, several tile sizes, tiles that are all zero, and states far from
+    unit norm (the exponent is per tile, so the relative error must not
+    depend on the scale)."""
+    rng = np.random.default_rng(63)
+    h = random_klocal(15, 50, rng, weights=(2, 3, 4))
+    for rule in (0, 1, 2):
+        _check(sd, h, _rand_state(rng, 15), 0.05, 2, 2, "c128", skip_rule=rule, jit=1)
+    for K in (10, 11):
+        _check(sd, h, _rand_state(rng, 15), 0.05, 5, 1, "c128", tile_bits=K, jit=1)
+    hj = jw_like(n=15, m=600, rng=rng)
+    _check(sd, hj, basis_state(15, (1 << 7) - 1), 0.05, 3, 2, "c128", jit=1)
+    groups = P.greedy_partition(h.x, h.z)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(jit=1)
+    for scale in (1e-30, 1e-3, 1e3, 1e30):
+        psi0 = _rand_state(rng, 15) * scale
+        ref = oracle.evolve(h, psi0, 0.05, 3, 1, groups)
+        t = _dev(psi0, "c128")
+        sim.evolve(t, 0.05, 3, 1)
+        err = np.linalg.norm(_host(t) - ref) / scale
+        assert err <= TOL["c128"], (scale, err)
+
+
 def test_jit_gradient(sd):
     rng = np.random.default_rng(62)
     n = 14
