@@ -44,6 +44,8 @@ def parse():
                     choices=["heisenberg30", "heisenberg32", "tfim10", "batch", "jw26", "grad24"],
                     help="heisenberg30 is the benchmark line; the others measure the remaining "
                          "configurations and print their own line")
+    ap.add_argument("--state", default="c64", choices=["c64", "c128"],
+                    help="state precision of the timed leg (c64 is the benchmark line)")
     ap.add_argument("--qubits", type=int, default=30, choices=[16, 20, 24, 25, 28, 30],
                     help="lattice size: 30 is the benchmark workload (5x6); smaller lattices "
                          "are for profiler captures")
@@ -234,8 +236,11 @@ def main():
     h, neel, name = workload(args.qubits)
     n = h.n
     sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
-    st64 = sim.schedule_stats(sd.C64, 1)
-    launches = sim.count_passes(sd.C64, 1, args.steps)   # tile passes of the timed call
+    code = sd.C64 if args.state == "c64" else sd.C128
+    cdt = torch.complex64 if args.state == "c64" else torch.complex128
+    amp_bytes = 8 if args.state == "c64" else 16
+    st64 = sim.schedule_stats(code, 1)
+    launches = sim.count_passes(code, 1, args.steps)   # tile passes of the timed call
     stream = torch.cuda.current_stream()
     N = 1 << n
 
@@ -245,8 +250,8 @@ def main():
         return s
 
     # ---------------------------------------------------------------- main leg
-    state = fresh(torch.complex64)
-    sim.prepare(sd.C64, DT, args.steps, 1)    # programs of the timed call (run-time compilation)
+    state = fresh(cdt)
+    sim.prepare(code, DT, args.steps, 1)      # programs of the timed call (run-time compilation)
     sim.evolve(state, DT, args.warmup, 1)
     torch.cuda.synchronize()
     barrier(ws)
@@ -266,22 +271,25 @@ def main():
     norm_err = abs(float(torch.linalg.vector_norm(state.to(torch.complex128)).item()) - 1.0)
 
     peak, peak_kind = peaks()
-    bytes_per_pass = 2 * N * 8
+    bytes_per_pass = 2 * N * amp_bytes
     avg_launch_s = t / launches
     achieved = bytes_per_pass / avg_launch_s / 1e9
     out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.state,
            "data": "synthetic",
            "config": {"workload": name, "n": n, "terms": h.m, "groups": 3, "dt": DT, "order": 1,
-                      "initial": "neel", "state": "complex64, Q0.64 phase angles",
+                      "initial": "neel",
+                      "state": ("complex64, Q0.64 phase angles" if args.state == "c64" else
+                                "complex128, 64-bit fixed point in the passes, Q0.64 phase angles"),
                       "l2": "state 8 GiB > 129 MB L2, no flush needed" if n == 30 else "small",
                       "parallelism": f"replicas x{ws}", "tile_bits": st64["tile_bits"],
                       "passes_per_step": launches / args.steps,
                       "passes_per_single_step": st64["passes_per_step"]},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(n),
-                        "kernel": "sd_pass_c64_* (one generated kernel per tile pass, "
+                        "frac": achieved / peak,
+                        "traffic": TRAFFIC_PER_LAUNCH.get(n) if args.state == "c64" else None,
+                        "kernel": f"sd_pass_{args.state}_* (one generated kernel per tile pass, "
                                   f"{launches} launches in {args.steps} steps; achieved = mean over them)",
                         "peak_kind": f"{peak_kind} copy bandwidth",
                         "bytes_per_launch": bytes_per_pass},
