@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip per-Pauli / c128 / e2e legs")
     ap.add_argument("--workload", default="heisenberg30",
-                    choices=["heisenberg30", "heisenberg32", "tfim10", "batch", "jw26", "grad24"],
+                    choices=["heisenberg30", "heisenberg32", "tfim10", "batch", "jw26", "grad24",
+                             "tfim_fc", "syk", "sweep"],
                     help="heisenberg30 is the benchmark line; the others measure the remaining "
                          "configurations and print their own line")
     ap.add_argument("--state", default="c64", choices=["c64", "c128"],

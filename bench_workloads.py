@@ -154,6 +154,66 @@ def grad24(args):
           grad_norm=float(np.linalg.norm(g)))
 
 
+def _grouped_vs_pauli(h, dt, steps, state_index=0, order=1):
+    """Steps/s of the grouped path and of the per-Pauli path on one state
+    (complex64), both after a warm-up call; returns a dict."""
+    import torch
+    import paper_2206_11664_gb300 as sd
+    t0 = time.perf_counter()
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    plan_s = time.perf_counter() - t0
+    groups = sim.plan_view()["n_groups"]
+    psi = torch.zeros(1 << h.n, dtype=torch.complex64, device="cuda")
+    psi[state_index] = 1
+    sim.prepare(sd.C64, dt, steps, order)
+    sim.evolve(psi, dt, 1, order)
+    t = _time(lambda: sim.evolve(psi, dt, steps, order))
+    ps = max(1, steps // 4)
+    sim.evolve_pauli(psi, dt, 1, order)
+    tp = _time(lambda: sim.evolve_pauli(psi, dt, ps, order))
+    passes = sim.count_passes(sd.C64, order, steps)
+    return {"n": h.n, "terms": h.m, "groups": groups, "theory_m_over_n_ng": h.m / (h.n * groups),
+            "steps_per_s": steps / t, "per_pauli_steps_per_s": ps / tp,
+            "speedup": (steps / t) / (ps / tp), "passes_per_step": passes / steps,
+            "ms_per_step": 1e3 * t / steps, "plan_s": plan_s}
+
+
+def tfim_fc(args):
+    """Fully connected transverse-field Ising model (the paper's first
+    experiment), n = 30, J_ij, h_i ~ U[-1, 1], |0..0>, dt = 0.01, complex64,
+    first order: grouped vs per-Pauli on the same GPU."""
+    from workloads import tfim_fully_connected
+    r = _grouped_vs_pauli(tfim_fully_connected(30), 0.01, max(4, args.steps))
+    _line("fully connected TFIM n=30 Trotter steps/s (grouped; per-Pauli beside it)", r["steps_per_s"],
+          "steps/s", {"workload": "tfim_fully_connected_n30", "dt": 0.01, "order": 1, "state": "complex64"},
+          **r)
+
+
+def syk(args):
+    """SYK Majorana model (the paper's second experiment), n = 20 qubits
+    (40 Majorana operators, 91390 terms), |0..0>, dt = 0.01, complex64, first
+    order: grouped vs per-Pauli on the same GPU."""
+    from workloads import syk_majorana
+    r = _grouped_vs_pauli(syk_majorana(20), 0.01, 2)
+    _line("SYK n=20 Trotter steps/s (grouped; per-Pauli beside it)", r["steps_per_s"], "steps/s",
+          {"workload": "syk_majorana_n20", "dt": 0.01, "order": 1, "state": "complex64"}, **r)
+
+
+def sweep(args):
+    """Speedup of the grouped path over the per-Pauli path against n for the
+    paper's two models (its Figs. 5-6 compare the same two methods against
+    the cost model m/(n n_g)); one line per point."""
+    from workloads import syk_majorana, tfim_fully_connected
+    for n in (14, 18, 22, 26, 30):
+        r = _grouped_vs_pauli(tfim_fully_connected(n), 0.01, 8)
+        _line(f"fully connected TFIM n={n}: grouped vs per-Pauli", r["speedup"], "x",
+              {"workload": f"tfim_fully_connected_n{n}", "dt": 0.01, "state": "complex64"}, **r)
+    for n in (14, 16, 18, 20):
+        r = _grouped_vs_pauli(syk_majorana(n), 0.01, 2)
+        _line(f"SYK n={n}: grouped vs per-Pauli", r["speedup"], "x",
+              {"workload": f"syk_majorana_n{n}", "dt": 0.01, "state": "complex64"}, **r)
+
+
 def run(args):
     {"heisenberg32": heisenberg32, "tfim10": tfim10, "batch": batch, "jw26": jw26,
-     "grad24": grad24}[args.workload](args)
+     "grad24": grad24, "tfim_fc": tfim_fc, "syk": syk, "sweep": sweep}[args.workload](args)

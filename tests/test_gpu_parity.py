@@ -12,6 +12,7 @@ import oracle
 from oracle import planner as P
 from workloads import (from_strings, heisenberg_lattice, jw_like, neel_index, random_klocal,
                        tfim_chain, basis_state, plus_state, product_state, haar_product_factors,
+                       tfim_fully_connected, syk_majorana,
                        gradient_2local, z_average_observable, batch_instances)
 
 pytestmark = pytest.mark.gpu
@@ -134,6 +135,28 @@ def test_tile_jw_like(sd):
     psi0 = basis_state(15, (1 << 7) - 1)
     _check(sd, h, psi0, 0.05, 3, 2, "c128")
     _check(sd, h, psi0, 0.05, 3, 2, "c64")
+
+
+def test_paper_models(sd):
+    """The paper's two experiment Hamiltonians (Sec. 4): the fully connected
+    transverse-field Ising model (2 groups, 10 steps on the tile path, both
+    precisions) and the SYK Majorana model on 14 qubits (20475 terms, 816
+    groups, tile path)."""
+    rng = np.random.default_rng(64)
+    h = tfim_fully_connected(16, rng)
+    for dtype in ("c128", "c64"):
+        _check(sd, h, _rand_state(rng, 16), 0.02, 10, 1, dtype)
+    hs = syk_majorana(14, rng)
+    groups = P.greedy_partition(hs.x, hs.z)      # one oracle grouping for both checks
+    sim = sd.Simulator(hs.n, hs.x, hs.z, hs.c).plan()
+    assert sim.plan_view()["n_groups"] == len(groups)
+    for dtype, order in (("c128", 1), ("c64", 2)):
+        psi0 = _rand_state(rng, 14)
+        ref = oracle.evolve(hs, psi0, 0.01, 1, order, groups)
+        t = _dev(psi0, dtype)
+        sim.evolve(t, 0.01, 1, order)
+        err = np.linalg.norm(_host(t) - ref)
+        assert err <= TOL[dtype], (dtype, err)
 
 
 def test_tile_gradient_hamiltonian_plus_state(sd):

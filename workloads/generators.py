@@ -23,6 +23,7 @@ __all__ = [
     "Hamiltonian", "pauli_to_masks", "masks_to_pauli", "from_strings",
     "tfim_chain", "heisenberg_lattice", "lattice_sites", "neel_index",
     "random_klocal", "batch_instances", "jw_like", "gradient_2local",
+    "tfim_fully_connected", "majorana_strings", "syk_majorana",
     "product_state", "haar_product_factors", "plus_state", "basis_state",
     "z_average_observable", "SEED_BASE", "BATCH_SEED_BASE",
 ]
@@ -213,6 +214,76 @@ def gradient_2local(n: int = 24, m: int = 200,
     h = _build(n, terms)
     h.c[:] = rng.uniform(-1.0, 1.0, size=m)
     return h
+
+
+def tfim_fully_connected(n: int = 30, rng: np.random.Generator | None = None) -> Hamiltonian:
+    """Fully connected transverse-field Ising model of the paper's first
+    experiment (Sec. 4): H = sum_{i<j} J_ij Z_i Z_j + sum_i h_i X_i with J_ij
+    and h_i uniform in [-1, 1]; the ZZ terms (pairs in lexicographic order)
+    come first, then the X terms, so first-fit grouping gives 2 groups of
+    n(n-1)/2 and n terms."""
+    if rng is None:
+        rng = np.random.default_rng(SEED_BASE + 5)
+    terms = [({i: "Z", j: "Z"}, 0.0) for i in range(n) for j in range(i + 1, n)]
+    terms += [({i: "X"}, 0.0) for i in range(n)]
+    h = _build(n, terms)
+    h.c[:] = rng.uniform(-1.0, 1.0, size=h.m)
+    return h
+
+
+def majorana_strings(n: int):
+    """The 2n Majorana operators of n qubits in the Jordan-Wigner form of the
+    paper's second experiment (Sec. 4), as (x, z) masks: operator 2q is
+    Z_0 ... Z_{q-1} X_q and operator 2q + 1 is Z_0 ... Z_{q-1} Y_q (the
+    paper's c_{2i-1}, c_{2i} with qubit i = q + 1)."""
+    out = []
+    for q in range(n):
+        low = (1 << q) - 1
+        out.append((1 << q, low))
+        out.append((1 << q, low | (1 << q)))
+    return out
+
+
+def _pauli_product(a, b):
+    """P_a P_b = i^k P_(xa^xb, za^zb) for Hermitian Pauli strings in the
+    (x, z) encoding (Y = i X Z on a qubit); returns (x, z, k mod 4)."""
+    (xa, za), (xb, zb) = a, b
+    x, z = xa ^ xb, za ^ zb
+    k = (bin(xa & za).count("1") + bin(xb & zb).count("1") + 2 * bin(za & xb).count("1")
+         - bin(x & z).count("1")) % 4
+    return x, z, k
+
+
+def syk_majorana(n: int = 10, rng: np.random.Generator | None = None) -> Hamiltonian:
+    """SYK Majorana model of the paper's second experiment (Sec. 4) on n
+    qubits (N = 2n Majorana operators): H = sum_{i<j<k<l} J_ijkl c_i c_j c_k
+    c_l with c from ``majorana_strings`` and real J_ijkl ~ N(0, 1), in
+    lexicographic (i, j, k, l) order; C(2n, 4) terms.  The paper draws complex
+    J with J_ijkl = J*_lkji, which is inconsistent for distinct indices: the
+    product of four distinct Majorana operators is Hermitian, so a Hermitian H
+    needs real coefficients.  Each product is +-1 times one Pauli string; the
+    sign goes into the coefficient."""
+    if rng is None:
+        rng = np.random.default_rng(SEED_BASE + 6)
+    maj = majorana_strings(n)
+    N = 2 * n
+    xs, zs, sg = [], [], []
+    for i in range(N):
+        for j in range(i + 1, N):
+            xij, zij, kij = _pauli_product(maj[i], maj[j])
+            for k in range(j + 1, N):
+                x3, z3, k3 = _pauli_product((xij, zij), maj[k])
+                for l in range(k + 1, N):
+                    x4, z4, k4 = _pauli_product((x3, z3), maj[l])
+                    ph = (kij + k3 + k4) % 4
+                    if ph % 2:
+                        raise AssertionError("a product of four Majorana operators is Hermitian")
+                    xs.append(x4)
+                    zs.append(z4)
+                    sg.append(1.0 if ph == 0 else -1.0)
+    J = rng.standard_normal(len(xs))
+    return Hamiltonian(n, np.array(xs, dtype=np.uint64), np.array(zs, dtype=np.uint64),
+                       J * np.array(sg))
 
 
 def z_average_observable(n: int):
