@@ -195,10 +195,24 @@ sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt,
  * each; the others are grouped by tile size and advanced pass level by pass
  * level, one launch per level covering every problem of the group, with the
  * blocks of a launch shared among the problems in proportion to their
- * sizes.  Asynchronous on the stream; at most 65535 problems. */
+ * sizes.  Asynchronous on the stream; at most 65535 problems.  The first
+ * call with given (ctxs, d_states, dtype, dt, steps, order) builds the
+ * programs and the device descriptors of the batch synchronously; repeated
+ * calls reuse them and only launch kernels, so such a call can be captured
+ * into a CUDA graph.  Under stream capture a batch that is not prepared
+ * gives SD_EINVAL.  The descriptors are dropped when a context of the batch
+ * frees its programs (another dt, sd_set_coeffs, sd_plan, sd_destroy); the
+ * library keeps those of the 8 most recent batches. */
 sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t count,
                           sd_dtype dtype, double dt, int64_t steps, int order,
                           void *cuda_stream);
+
+/* Builds, without launching anything, the programs and device descriptors
+ * that sd_evolve_batch with the same arguments uses (for example before
+ * capturing that call into a CUDA graph).  Synchronous; errors as for
+ * sd_evolve_batch. */
+sd_status sd_prepare_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t count,
+                           sd_dtype dtype, double dt, int64_t steps, int order);
 
 /* <psi|O|psi> like sd_expect, for callers that cannot allocate device
  * memory (a fixed budget owned by another allocator, or a loop that must not

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _native as N
 
-__all__ = ["Simulator", "SDError", "evolve_batch", "TrotterExpectation", "C64", "C128"]
+__all__ = ["Simulator", "SDError", "evolve_batch", "prepare_batch", "TrotterExpectation", "C64", "C128"]
 
 C64, C128 = N.SD_C64, N.SD_C128
 
@@ -215,20 +215,38 @@ class Simulator:
         return f.value, g
 
 
-def evolve_batch(sims, states, dt, steps, order=1, stream=None):
-    """Evolve independent problems (each planned, own state) in one call."""
+def _batch_args(sims, states):
     if len(sims) != len(states):
         raise ValueError("one state per simulator")
-    if not sims:
-        return
-    lib = sims[0]._lib
     dts = {_dtype_of(s) for s in states}
     if len(dts) != 1:
         raise ValueError("all states must have the same dtype")
     hs = (ctypes.c_void_p * len(sims))(*[s._h for s in sims])
     ps = (ctypes.c_void_p * len(states))(*[s.data_ptr() for s in states])
-    st = lib.sd_evolve_batch(hs, ps, len(sims), dts.pop(), float(dt), int(steps), int(order),
+    return hs, ps, dts.pop()
+
+
+def evolve_batch(sims, states, dt, steps, order=1, stream=None):
+    """Evolve independent problems (each planned, own state) in one call.
+    A repeated call with the same problems, states and arguments only
+    launches kernels (capturable in a CUDA graph)."""
+    if not sims:
+        return
+    lib = sims[0]._lib
+    hs, ps, dt_code = _batch_args(sims, states)
+    st = lib.sd_evolve_batch(hs, ps, len(sims), dt_code, float(dt), int(steps), int(order),
                              _stream(stream))
+    if st != N.SD_OK:
+        raise SDError(st, lib.sd_last_error(None).decode())
+
+
+def prepare_batch(sims, states, dt, steps, order=1):
+    """Build (no launch) what evolve_batch with these arguments runs."""
+    if not sims:
+        return
+    lib = sims[0]._lib
+    hs, ps, dt_code = _batch_args(sims, states)
+    st = lib.sd_prepare_batch(hs, ps, len(sims), dt_code, float(dt), int(steps), int(order))
     if st != N.SD_OK:
         raise SDError(st, lib.sd_last_error(None).decode())
 

@@ -56,6 +56,8 @@ SIGNATURES = {
                         P_dbl, P_dbl, c_vp]),
     "sd_evolve_batch": (c_int, [ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_i64, c_int, c_dbl,
                                 c_i64, c_int, c_vp]),
+    "sd_prepare_batch": (c_int, [ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_i64, c_int, c_dbl,
+                                 c_i64, c_int]),
     "sd_expect_noalloc": (c_int, [c_int, c_vp, c_int, c_i64, P_u64, P_u64, P_dbl, P_dbl, c_vp]),
     "sd_last_error": (ctypes.c_char_p, [c_vp]),
     "sd_destroy": (None, [c_vp]),

@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <list>
 #include <memory>
 #include <string>
 #include <tuple>
@@ -50,6 +52,10 @@ void free_program(Program &p) {
 
 }  // namespace
 
+namespace {
+void batch_purge(const sd_ctx *ctx);
+}
+
 struct sd_ctx {
     int n = 0;
     int64_t m = 0;
@@ -83,6 +89,7 @@ struct sd_ctx {
     double grad_dt = 0.0;
 
     ~sd_ctx() {
+        batch_purge(this);
         for (auto &kv : programs) free_program(*kv.second);
         for (auto &kv : cliff_programs) free_program(*kv.second);
         for (void *a : grad_allocs) cudaFree(a);
@@ -300,6 +307,7 @@ sd_status get_program(sd_ctx *ctx, bool dbl, int order, int kind, double dt, Pro
     // keep the cache small: programs for other dt values are dropped
     for (auto i = ctx->programs.begin(); i != ctx->programs.end();) {
         if (std::get<3>(i->first) != dt) {
+            batch_purge(ctx);
             free_program(*i->second);
             i = ctx->programs.erase(i);
         } else {
@@ -647,6 +655,7 @@ sd_status sd_set_coeffs(sd_ctx *ctx, const double *coeffs) {
         if (!std::isfinite(coeffs[j]))
             return fail(ctx, SD_EINVAL, "term " + std::to_string(j) + " has a non-finite coefficient");
     ctx->c.assign(coeffs, coeffs + ctx->m);
+    batch_purge(ctx);
     for (auto &kv : ctx->programs) free_program(*kv.second);
     ctx->programs.clear();
     for (void *p : ctx->grad_allocs) cudaFree(p);
@@ -668,6 +677,7 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     Plan p;
     std::string e = make_plan(ctx->n, ctx->m, ctx->x.data(), ctx->z.data(), rule, p);
     if (!e.empty()) return fail(ctx, SD_EINTERNAL, "planner: " + e);
+    batch_purge(ctx);
     for (auto &kv : ctx->programs) free_program(*kv.second);
     ctx->programs.clear();
     for (auto &kv : ctx->cliff_programs) free_program(*kv.second);
@@ -943,33 +953,76 @@ sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt, 
     return SD_OK;
 }
 
-sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t count, sd_dtype dtype,
-                          double dt, int64_t steps, int order, void *cuda_stream) {
-    sd_ctx *ctx = nullptr;
-    if (!ctxs || !d_states || count < 0) return fail(nullptr, SD_EINVAL, "invalid batch arguments");
-    if (count > 65535) return fail(nullptr, SD_EINVAL, "at most 65535 instances per batch");
-    if (steps < 0 || !std::isfinite(dt)) return fail(nullptr, SD_EINVAL, "invalid steps or dt");
-    for (int64_t i = 0; i < count; i++) {
-        sd_status s = check_state_args(ctxs[i], d_states[i], dtype, order);
-        if (s != SD_OK) return s;
+}  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------ batch descriptors
+// The device descriptors of an sd_evolve_batch call (each instance's
+// programs and share of blocks) are kept for reuse, so that a repeated call
+// copies nothing from the host and can be captured in a CUDA graph.  An
+// entry refers to its instances' programs, so it is dropped whenever one of
+// those contexts frees programs (another dt, new coefficients, a new plan,
+// sd_destroy).
+struct BatchGroup {
+    int K;
+    size_t smem;
+    int ctas;
+    int64_t levels;
+    BatchInstance *d_inst;
+    uint16_t *d_cta;
+};
+struct BatchEntry {
+    std::vector<sd_ctx *> ctxs;
+    std::vector<void *> states;
+    int dtype;
+    double dt;
+    int64_t steps;
+    int order;
+    std::vector<int64_t> alone;   // instances run one by one (on chip, or mixed tile sizes)
+    std::vector<BatchGroup> groups;
+};
+std::recursive_mutex g_batch_mu;
+std::list<BatchEntry> g_batches;   // most recent first
+constexpr size_t kBatchCache = 8;
+
+void free_batch(BatchEntry &e) {
+    for (auto &g : e.groups) {
+        cudaFree(g.d_inst);
+        cudaFree(g.d_cta);
     }
-    if (steps == 0 || count == 0) return SD_OK;
+}
+
+void batch_purge(const sd_ctx *ctx) {
+    std::lock_guard<std::recursive_mutex> lk(g_batch_mu);
+    for (auto it = g_batches.begin(); it != g_batches.end();) {
+        if (std::find(it->ctxs.begin(), it->ctxs.end(), ctx) != it->ctxs.end()) {
+            free_batch(*it);
+            it = g_batches.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// Finds or builds the descriptors of a batch call (programs included).
+// Building allocates and copies synchronously, so it is refused while `st`
+// is being captured.  Called with g_batch_mu held.
+sd_status batch_entry(sd_ctx *const *ctxs, void *const *d_states, int64_t count, sd_dtype dtype, double dt,
+                      int64_t steps, int order, cudaStream_t st, BatchEntry *&out) {
     const bool dbl = dtype == SD_C128;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    // Every instance's programs are built first; instances on the on-chip path
-    // run on their own (one launch each); the others are grouped by tile size
-    // and advanced level by level, one launch per level for the whole group.
     struct Item {
         sd_ctx *ctx;
         void *psi;
         Program *prog[3];
         int64_t reps;
+        int64_t index;
     };
-    std::map<int, std::vector<Item>> by_k;
+    std::vector<Item> items;
     for (int64_t i = 0; i < count; i++) {
-        ctx = ctxs[i];
+        sd_ctx *ctx = ctxs[i];
         const int G = (int)ctx->plan.groups.size();
-        Item it{ctx, d_states[i], {nullptr, nullptr, nullptr}, steps};
+        Item it{ctx, d_states[i], {nullptr, nullptr, nullptr}, steps, i};
         sd_status s;
         if (order == 1 || G == 1 || steps == 1) {
             if ((s = get_program(ctx, dbl, order, 0, dt, it.prog[1])) != SD_OK) return s;
@@ -979,6 +1032,29 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
             if ((s = get_program(ctx, dbl, order, 3, dt, it.prog[2])) != SD_OK) return s;
             it.reps = steps - 1;
         }
+        items.push_back(it);
+    }
+    for (auto &e : g_batches)
+        if (e.dtype == (int)dtype && e.dt == dt && e.steps == steps && e.order == order &&
+            e.ctxs.size() == (size_t)count && std::equal(e.ctxs.begin(), e.ctxs.end(), ctxs) &&
+            std::equal(e.states.begin(), e.states.end(), d_states)) {
+            out = &e;
+            return SD_OK;
+        }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+        return fail(ctxs[0], SD_EINVAL,
+                    "sd_evolve_batch under stream capture needs its descriptors built first: call "
+                    "sd_prepare_batch (or the same sd_evolve_batch) outside the capture");
+    BatchEntry e;
+    e.ctxs.assign(ctxs, ctxs + count);
+    e.states.assign(d_states, d_states + count);
+    e.dtype = (int)dtype;
+    e.dt = dt;
+    e.steps = steps;
+    e.order = order;
+    std::map<int, std::vector<Item>> by_k;
+    for (auto &it : items) {
         int K = -1;
         bool mixed = false;
         for (Program *p : it.prog) {
@@ -988,18 +1064,21 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
             else if (K != p->sched.K) mixed = true;
         }
         if (mixed || K < 0) {
-            if ((s = evolve_impl(ctx, it.psi, dbl, dt, steps, order, st)) != SD_OK) return s;
-            continue;
+            // run like sd_evolve; build its block programs now
+            sd_status s = evolve_impl(it.ctx, it.psi, dbl, dt, steps, order, st, false);
+            if (s != SD_OK) return s;
+            e.alone.push_back(it.index);
+        } else {
+            by_k[K].push_back(it);
         }
-        by_k[K].push_back(it);
     }
     for (auto &kv : by_k) {
         const int K = kv.first;
-        std::vector<Item> &items = kv.second;
-        ctx = items[0].ctx;
+        std::vector<Item> &grp = kv.second;
+        sd_ctx *ctx = grp[0].ctx;
         int64_t total_tiles = 0;
         size_t smem = 0;
-        for (auto &it : items) {
+        for (auto &it : grp) {
             total_tiles += (int64_t)1 << (it.ctx->n - K);
             for (Program *p : it.prog)
                 if (p)
@@ -1008,11 +1087,11 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
         if (smem > kTileSmemLimit) return fail(ctx, SD_EINTERNAL, "batch pass needs too much shared memory");
         const int occ = tile_pass_batch_occupancy(dbl, K, smem);
         const int64_t target = (int64_t)ctx->num_sms * occ * 2;
-        std::vector<BatchInstance> inst(items.size());
+        std::vector<BatchInstance> inst(grp.size());
         std::vector<uint16_t> cta;
         int64_t max_levels = 0;
-        for (size_t i = 0; i < items.size(); i++) {
-            const Item &it = items[i];
+        for (size_t i = 0; i < grp.size(); i++) {
+            const Item &it = grp[i];
             const int64_t tiles = (int64_t)1 << (it.ctx->n - K);
             int64_t c = (target * tiles + total_tiles - 1) / total_tiles;
             c = std::max<int64_t>(1, std::min(c, tiles));
@@ -1037,17 +1116,73 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
             max_levels = std::max(max_levels, B.levels);
             for (int64_t j = 0; j < c; j++) cta.push_back((uint16_t)i);
         }
-        BatchInstance *d_inst = nullptr;
-        uint16_t *d_cta = nullptr;
-        CK(cudaMallocAsync((void **)&d_inst, sizeof(BatchInstance) * inst.size(), st));
-        CK(cudaMallocAsync((void **)&d_cta, sizeof(uint16_t) * cta.size(), st));
-        CK(cudaMemcpyAsync(d_inst, inst.data(), sizeof(BatchInstance) * inst.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(d_cta, cta.data(), sizeof(uint16_t) * cta.size(), cudaMemcpyHostToDevice, st));
-        for (int64_t L = 0; L < max_levels; L++)
-            CK(launch_tile_pass_batch(dbl, K, d_inst, d_cta, (int)cta.size(), smem, L, st));
-        CK(cudaFreeAsync(d_inst, st));
-        CK(cudaFreeAsync(d_cta, st));   // pageable-source copies are staged before they return
+        BatchGroup g{K, smem, (int)cta.size(), max_levels, nullptr, nullptr};
+        e.groups.push_back(g);   // freed with the entry if an allocation below fails
+        BatchGroup &gg = e.groups.back();
+        cudaError_t ce = cudaMalloc((void **)&gg.d_inst, sizeof(BatchInstance) * inst.size());
+        if (ce == cudaSuccess) ce = cudaMalloc((void **)&gg.d_cta, sizeof(uint16_t) * cta.size());
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(gg.d_inst, inst.data(), sizeof(BatchInstance) * inst.size(), cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(gg.d_cta, cta.data(), sizeof(uint16_t) * cta.size(), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            free_batch(e);
+            return fail(ctx, SD_ECUDA, std::string("batch descriptors: ") + cudaGetErrorString(ce));
+        }
     }
+    g_batches.push_front(std::move(e));
+    while (g_batches.size() > kBatchCache) {
+        free_batch(g_batches.back());
+        g_batches.pop_back();
+    }
+    out = &g_batches.front();
+    return SD_OK;
+}
+
+sd_status batch_args(sd_ctx *const *ctxs, void *const *d_states, int64_t count, sd_dtype dtype, double dt,
+                     int64_t steps, int order) {
+    if (!ctxs || !d_states || count < 0) return fail(nullptr, SD_EINVAL, "invalid batch arguments");
+    if (count > 65535) return fail(nullptr, SD_EINVAL, "at most 65535 instances per batch");
+    if (steps < 0 || !std::isfinite(dt)) return fail(nullptr, SD_EINVAL, "invalid steps or dt");
+    for (int64_t i = 0; i < count; i++) {
+        sd_status s = check_state_args(ctxs[i], d_states[i], dtype, order);
+        if (s != SD_OK) return s;
+    }
+    return SD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sd_status sd_prepare_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t count, sd_dtype dtype,
+                           double dt, int64_t steps, int order) {
+    sd_status s = batch_args(ctxs, d_states, count, dtype, dt, steps, order);
+    if (s != SD_OK || steps == 0 || count == 0) return s;
+    std::lock_guard<std::recursive_mutex> lk(g_batch_mu);
+    BatchEntry *e = nullptr;
+    return batch_entry(ctxs, d_states, count, dtype, dt, steps, order, nullptr, e);
+}
+
+sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t count, sd_dtype dtype,
+                          double dt, int64_t steps, int order, void *cuda_stream) {
+    sd_status s = batch_args(ctxs, d_states, count, dtype, dt, steps, order);
+    if (s != SD_OK || steps == 0 || count == 0) return s;
+    const bool dbl = dtype == SD_C128;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::recursive_mutex> lk(g_batch_mu);
+    BatchEntry *e = nullptr;
+    if ((s = batch_entry(ctxs, d_states, count, dtype, dt, steps, order, st, e)) != SD_OK) return s;
+    // Instances on the on-chip path (or with mixed tile sizes) run one by one;
+    // the others advance level by level, one launch per level for each tile size.
+    for (int64_t i : e->alone)
+        if ((s = evolve_impl(ctxs[i], d_states[i], dbl, dt, steps, order, st)) != SD_OK) return s;
+    for (auto &g : e->groups)
+        for (int64_t L = 0; L < g.levels; L++) {
+            cudaError_t ce = launch_tile_pass_batch(dbl, g.K, g.d_inst, g.d_cta, g.ctas, g.smem, L, st);
+            if (ce != cudaSuccess)
+                return fail(ctxs[0], SD_ECUDA, std::string("batch launch: ") + cudaGetErrorString(ce));
+        }
     return SD_OK;
 }
 

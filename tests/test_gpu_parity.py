@@ -259,6 +259,52 @@ def test_batch_matches_individual(sd):
         assert np.linalg.norm(_host(t) - r) < 1e-4
 
 
+def test_cuda_graph_capture(sd):
+    """Once its programs are built, sd_evolve only launches kernels, and so
+    does a prepared sd_evolve_batch: both are captured into a CUDA graph and
+    replayed, and must give exactly what the same calls give eagerly."""
+    import torch
+    rng = np.random.default_rng(65)
+    h = heisenberg_lattice(4, 5)                       # n = 20: passes compiled at run time
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    psi0 = _rand_state(rng, h.n)
+    ref = _dev(psi0, "c64")
+    for _ in range(2):
+        sim.evolve(ref, 0.02, 5, 1)
+    t = _dev(psi0, "c64")
+    sim.prepare(sd.C64, 0.02, 5, 1)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        sim.evolve(t, 0.02, 5, 1)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(t, ref)
+
+    hs = [random_klocal(n, 60, rng, weights=(2, 3)) for n in (12, 15, 17)]   # on chip and tile path
+    sims = [sd.Simulator(x.n, x.x, x.z, x.c).plan() for x in hs]
+    psis = [_rand_state(rng, x.n) for x in hs]
+    refs = [_dev(p, "c128") for p in psis]
+    for _ in range(2):
+        sd.evolve_batch(sims, refs, 0.03, 3, 2)
+    ts = [_dev(p, "c128") for p in psis]
+    sd.prepare_batch(sims, ts, 0.03, 3, 2)
+    gb = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gb):
+        sd.evolve_batch(sims, ts, 0.03, 3, 2)
+    for _ in range(2):
+        gb.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(ts, refs):
+        assert torch.equal(a, b)
+    # capturing a batch whose descriptors were not built is refused, not run
+    other = [_dev(p, "c128") for p in psis]
+    g2 = torch.cuda.CUDAGraph()
+    with pytest.raises(sd.SDError):
+        with torch.cuda.graph(g2):
+            sd.evolve_batch(sims, other, 0.03, 3, 2)
+
+
 def test_invalid_state_rejected(sd):
     import torch
     h = tfim_chain(10)
