@@ -35,6 +35,8 @@ struct Program {
     DevCircuit circ;
     std::vector<void *> allocs;
     int64_t passes = 0, rounds = 0, diag_passes = 0;
+    // the pass launches of one repetition, as CUDA graphs, for up to 4 states
+    std::vector<std::pair<void *, cudaGraphExec_t>> graphs;
 };
 
 struct GradGroup {   // per (group, fraction): class-sorted terms for the adjoint kernel
@@ -46,6 +48,8 @@ struct GradGroup {   // per (group, fraction): class-sorted terms for the adjoin
 };
 
 void free_program(Program &p) {
+    for (auto &g : p.graphs) cudaGraphExecDestroy(g.second);
+    p.graphs.clear();
     for (void *a : p.allocs) cudaFree(a);
     p.allocs.clear();
 }
@@ -87,6 +91,7 @@ struct sd_ctx {
     size_t work_bytes = 0;
     double *d_gacc = nullptr;
     double grad_dt = 0.0;
+    cudaStream_t graph_stream = nullptr;   // private stream for capturing pass graphs
 
     ~sd_ctx() {
         batch_purge(this);
@@ -99,6 +104,7 @@ struct sd_ctx {
         cudaFree(d_work[0]);
         cudaFree(d_work[1]);
         cudaFree(d_gacc);
+        if (graph_stream) cudaStreamDestroy(graph_stream);
     }
 };
 
@@ -132,6 +138,44 @@ sd_status ensure_device(sd_ctx *ctx) {
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    return SD_OK;
+}
+
+// Constant rotation tables, one copy per device for the life of the process,
+// computed on the host in long double: e^{2 pi i k/256} in FP64, and the
+// Q1.62 tables of the fixed-point passes (e^{2 pi i k/256}, e^{2 pi i k/65536}).
+struct DevTables {
+    double2 *tw = nullptr;
+    longlong2 *fxt = nullptr;
+};
+std::mutex g_tab_mu;
+std::map<int, DevTables> g_tabs;
+
+sd_status device_tables(sd_ctx *ctx, DevTables &out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto it = g_tabs.find(dev);
+    if (it != g_tabs.end()) {
+        out = it->second;
+        return SD_OK;
+    }
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<double2> tw(256);
+    std::vector<longlong2> fxt(512);
+    for (int k = 0; k < 256; k++) {
+        const long double a = 2.0L * pi * k / 256.0L, b = 2.0L * pi * k / 65536.0L;
+        tw[k] = make_double2((double)cosl(a), (double)sinl(a));
+        fxt[k] = make_longlong2(llroundl(ldexpl(cosl(a), 62)), llroundl(ldexpl(sinl(a), 62)));
+        fxt[256 + k] = make_longlong2(llroundl(ldexpl(cosl(b), 62)), llroundl(ldexpl(sinl(b), 62)));
+    }
+    DevTables t;
+    CK(cudaMalloc((void **)&t.tw, sizeof(double2) * tw.size()));
+    CK(cudaMalloc((void **)&t.fxt, sizeof(longlong2) * fxt.size()));
+    CK(cudaMemcpy(t.tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.fxt, fxt.data(), sizeof(longlong2) * fxt.size(), cudaMemcpyHostToDevice));
+    g_tabs[dev] = t;
+    out = t;
     return SD_OK;
 }
 
@@ -217,6 +261,10 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
     sd_status ss = schedule_for(ctx, circ, dbl, S);
     if (ss != SD_OK) return ss;
     DevSchedule &D = P.sched;
+    DevTables tabs;
+    if ((ss = device_tables(ctx, tabs)) != SD_OK) return ss;
+    D.tw = tabs.tw;
+    D.fxt = tabs.fxt;
     D.K = S.K;
     D.c = S.c;
     D.n_passes = (int64_t)S.passes.size();
@@ -326,6 +374,25 @@ sd_status get_program(sd_ctx *ctx, bool dbl, int order, int kind, double dt, Pro
     return SD_OK;
 }
 
+// States up to this size run their pass sequences as CUDA graphs.
+constexpr size_t kGraphMaxStateBytes = (size_t)256 << 20;
+
+// The pass launches of one repetition of a tile-path program.
+sd_status launch_passes(sd_ctx *ctx, bool dbl, Program &P, void *psi, cudaStream_t st) {
+    if (P.jit.ok()) {
+        const KParams kp{P.sched.passes, P.sched.rounds, P.sched.ops, P.sched.perms, P.sched.diags,
+                         P.sched.phases, P.sched.term_mo, P.sched.slots, P.sched.term_q,
+                         P.sched.mask_pool, P.sched.cst_mo, P.sched.cst_q, P.sched.c,
+                         P.sched.tw, P.sched.fxt};
+        for (int64_t p = 0; p < P.sched.n_passes; p++)
+            CK(jit_launch(P.jit, (int)p, psi, kp, ctx->n, ctx->num_sms, st));
+        return SD_OK;
+    }
+    for (int64_t p = 0; p < P.sched.n_passes; p++)
+        CK(launch_tile_pass(dbl, psi, ctx->n, P.sched, (int)p, ctx->num_sms, st));
+    return SD_OK;
+}
+
 sd_status run_program(sd_ctx *ctx, bool dbl, Program &P, void *psi, int64_t reps, cudaStream_t st,
                       const uint64_t *d_oz = nullptr, const double *d_oc = nullptr, int nobs = 0,
                       double *d_trace = nullptr) {
@@ -335,18 +402,49 @@ sd_status run_program(sd_ctx *ctx, bool dbl, Program &P, void *psi, int64_t reps
         CK(launch_onchip(dbl, psi, ctx->n, P.circ, reps, d_oz, d_oc, nobs, d_trace, st));
         return SD_OK;
     }
-    if (P.jit.ok()) {
-        const KParams kp{P.sched.passes, P.sched.rounds, P.sched.ops, P.sched.perms, P.sched.diags,
-                         P.sched.phases, P.sched.term_mo, P.sched.slots, P.sched.term_q,
-                         P.sched.mask_pool, P.sched.cst_mo, P.sched.cst_q, P.sched.c};
-        for (int64_t r = 0; r < reps; r++)
-            for (int64_t p = 0; p < P.sched.n_passes; p++)
-                CK(jit_launch(P.jit, (int)p, psi, kp, ctx->n, ctx->num_sms, st));
-        return SD_OK;
+    // Small states make the passes launch-bound: their launches are then
+    // captured once into a CUDA graph (per program and state) and replayed.
+    const size_t state_bytes = ((size_t)1 << ctx->n) * (dbl ? 16 : 8);
+    bool use_graph = state_bytes <= kGraphMaxStateBytes && P.sched.n_passes >= 8;
+    if (use_graph) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            use_graph = false;   // the caller is capturing: launch into its graph directly
+        }
     }
-    for (int64_t r = 0; r < reps; r++)
-        for (int64_t p = 0; p < P.sched.n_passes; p++)
-            CK(launch_tile_pass(dbl, psi, ctx->n, P.sched, (int)p, ctx->num_sms, st));
+    cudaGraphExec_t graph = nullptr;
+    if (use_graph)
+        for (auto &g : P.graphs)
+            if (g.first == psi) graph = g.second;
+    if (use_graph && !graph) {
+        if (!ctx->graph_stream) CK(cudaStreamCreateWithFlags(&ctx->graph_stream, cudaStreamNonBlocking));
+        if (P.graphs.size() >= 4) {
+            cudaGraphExecDestroy(P.graphs.front().second);
+            P.graphs.erase(P.graphs.begin());
+        }
+        CK(cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeThreadLocal));
+        sd_status s = launch_passes(ctx, dbl, P, psi, ctx->graph_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(ctx->graph_stream, &g);
+        if (s != SD_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (ee != cudaSuccess) return fail(ctx, SD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+        const cudaError_t ie = cudaGraphInstantiate(&graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return fail(ctx, SD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+        P.graphs.push_back({psi, graph});
+    }
+    for (int64_t r = 0; r < reps; r++) {
+        if (use_graph) {
+            CK(cudaGraphLaunch(graph, st));
+        } else {
+            sd_status s = launch_passes(ctx, dbl, P, psi, st);
+            if (s != SD_OK) return s;
+        }
+    }
     return SD_OK;
 }
 
@@ -1108,7 +1206,7 @@ sd_status batch_entry(sd_ctx *const *ctxs, void *const *d_states, int64_t count,
                     B.kp[k] = KParams{p->sched.passes, p->sched.rounds, p->sched.ops, p->sched.perms,
                                       p->sched.diags, p->sched.phases, p->sched.term_mo, p->sched.slots,
                                       p->sched.term_q, p->sched.mask_pool, p->sched.cst_mo,
-                                      p->sched.cst_q, p->sched.c};
+                                      p->sched.cst_q, p->sched.c, p->sched.tw, p->sched.fxt};
                 else
                     B.kp[k] = KParams{};
             }

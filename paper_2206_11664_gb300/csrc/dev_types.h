@@ -10,6 +10,7 @@ typedef int int32_t;
 typedef unsigned char uint8_t;
 typedef decltype(sizeof(0)) size_t;
 #else
+#include <vector_types.h>
 #include <cstdint>
 #endif
 
@@ -165,6 +166,10 @@ struct KParams {
     const uint64_t *cst_mo;
     const int64_t *cst_q;
     int c;
+    // per-device constant tables: e^{2 pi i k/256} (FP64), and in Q1.62
+    // e^{2 pi i k/256} (entries 0..255) and e^{2 pi i k/65536} (256..511)
+    const double2 *tw;
+    const longlong2 *fxt;
 };
 
 }  // namespace sd

@@ -265,18 +265,17 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
       << "  __shared__ uint64_t CST[4];\n"
       << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n"
       << "  (void)lane; (void)warp;\n"
-      << "  for (int i = tid; i < 256; i += NT) {\n"
-      << "    double sn, cs;\n    sincospi((double)i / 128.0, &sn, &cs);\n";
+      << "  for (int i = tid; i < 256; i += NT) {\n";
     if (fx) {
-        const double q62 = 4611686018427387904.0, t1s = fx_res_table ? q62 * std::sqrt(0.5) : q62;
-        o << "    T1[i] = make_longlong2(__double2ll_rn(cs * " << dbl(t1s) << "), __double2ll_rn(sn * " << dbl(t1s)
-          << "));\n"
-          << "    sincospi((double)i / 32768.0, &sn, &cs);\n"
-          << "    T2[i] = make_longlong2(__double2ll_rn(cs * " << dbl(q62) << "), __double2ll_rn(sn * " << dbl(q62)
-          << "));\n";
+        if (fx_res_table)   // the pass's remaining 1/sqrt(2): x * (2^63/sqrt 2) / 2^64 * 2
+            o << "    { const longlong2 t = kp.fxt[i]; T1[i] = make_longlong2(__mul64hi(t.x, kRsqrt2Q63) << 1, "
+                 "__mul64hi(t.y, kRsqrt2Q63) << 1); }\n";
+        else
+            o << "    T1[i] = kp.fxt[i];\n";
+        o << "    T2[i] = kp.fxt[256 + i];\n";
     } else {
-        o << "    TW[i].x = (T)(cs * " << dbl(table_scale) << ");\n    TW[i].y = (T)(sn * " << dbl(table_scale)
-          << ");\n";
+        o << "    { const double2 e = kp.tw[i]; TW[i].x = (T)(e.x * " << dbl(table_scale) << "); TW[i].y = (T)(e.y * "
+          << dbl(table_scale) << "); }\n";
     }
     for (int byte = 0; byte < 4; byte++) {
         o << "    OUTT[" << byte << "][i] = 0ull";

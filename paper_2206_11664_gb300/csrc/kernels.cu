@@ -90,10 +90,9 @@ __device__ __forceinline__ void tile_pass_body(typename VT<T>::A *__restrict__ p
         swzc[tid] = col;
     }
     for (int i = tid; i < 256; i += NT) {
-        double sn, cs;
-        sincospi((double)i / 128.0, &sn, &cs);
-        TW[i].x = (T)cs;
-        TW[i].y = (T)sn;
+        const double2 e = kp.tw[i];
+        TW[i].x = (T)e.x;
+        TW[i].y = (T)e.y;
         uint64_t v = 0;
         for (int b = 0; b < 8 && b < K; b++)
             if ((i >> b) & 1) v |= (uint64_t)1 << P.tile_bits[b];
@@ -436,7 +435,7 @@ cudaError_t run_tile(void *psi, int n, const DevSchedule &S, int pass, int num_s
     if (e != cudaSuccess) return e;
     if (b < 1) b = 1;
     KParams kp{S.passes, S.rounds, S.ops, S.perms, S.diags, S.phases,
-               S.term_mo, S.slots, S.term_q, S.mask_pool, S.cst_mo, S.cst_q, S.c};
+               S.term_mo, S.slots, S.term_q, S.mask_pool, S.cst_mo, S.cst_q, S.c, S.tw, S.fxt};
     int64_t ntiles = (int64_t)1 << (n - K);
     int64_t grid = (int64_t)num_sms * b;
     if (grid > ntiles) grid = ntiles;

@@ -24,6 +24,8 @@ struct DevSchedule {
     uint64_t *mask_pool = nullptr;
     uint64_t *cst_mo = nullptr;
     int64_t *cst_q = nullptr;
+    const double2 *tw = nullptr;       // per-device constant tables (not owned)
+    const longlong2 *fxt = nullptr;
     std::vector<DevPass> host_passes;  // for launch-side decisions
 };
 
