@@ -142,6 +142,20 @@ sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_st
  * SD_EINVAL / SD_ENOPLAN as for sd_evolve. */
 sd_status sd_prepare(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order);
 
+/* Tile-size autotuner.  For each tile size K = kmin..kmax (9 <= kmin <=
+ * kmax <= 13; a tile is 2^K amplitudes staged in one block's shared memory),
+ * runs sd_evolve(., dt, steps, order) once to build and compile its programs
+ * and once timed with CUDA events, on a scratch state of 2^n amplitudes of
+ * `dtype` that the call allocates and frees (caller states are untouched).
+ * The fastest K is kept for this dtype and used by later calls of the
+ * context (a tile size given to sd_plan overrides it; sd_plan clears it).
+ * best_k (may be NULL) receives it; times_ms (may be NULL, kmax - kmin + 1
+ * doubles) receives milliseconds per step, 0 for sizes not run.  Sizes the
+ * scheduler cannot use are skipped.  On the on-chip path nothing is tuned
+ * (best_k = 0).  Synchronous; SD_ENOMEM if the scratch state does not fit. */
+sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin,
+                      int kmax, int *best_k, double *times_ms);
+
 /* Number of tile-pass kernels sd_evolve(ctx, ., dtype, ., steps, order, .)
  * launches; each reads and writes the state once.  0 when the state stays
  * on chip (one launch then runs every step).  A call of several steps merges

@@ -162,6 +162,18 @@ class Simulator:
         self._check(self._lib.sd_prepare(self._h, dtype, float(dt), int(steps), int(order)))
         return self
 
+    def autotune(self, dtype, dt, steps=4, order=1, kmin=None, kmax=None):
+        """Time tile sizes kmin..kmax on a scratch state and keep the fastest
+        for `dtype`; returns (best K, {K: ms per step}) (best K is 0 when the
+        state stays on chip)."""
+        kmax = 13 if kmax is None else int(kmax)
+        kmin = max(9, kmax - 2) if kmin is None else int(kmin)
+        best = ctypes.c_int(0)
+        times = np.zeros(kmax - kmin + 1)
+        self._check(self._lib.sd_autotune(self._h, dtype, float(dt), int(steps), int(order), kmin, kmax,
+                                          ctypes.byref(best), times.ctypes.data_as(N.P_dbl)))
+        return best.value, {kmin + i: float(t) for i, t in enumerate(times) if t > 0}
+
     def count_passes(self, dtype=C64, order=1, steps=1):
         """Tile-pass launches evolve() makes for `steps` steps (0 on chip)."""
         out = ctypes.c_int64(0)

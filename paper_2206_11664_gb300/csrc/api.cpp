@@ -68,6 +68,7 @@ struct sd_ctx {
     bool planned = false;
     Plan plan;
     int tile_bits_opt = 0;
+    int tuned_k[2] = {0, 0};   // tile size chosen by sd_autotune (complex64, complex128)
     int jit_opt = 0;
     std::string jit_note;    // why the last program did not use run-time specialisation
     // plan view storage
@@ -180,7 +181,8 @@ sd_status device_tables(sd_ctx *ctx, DevTables &out) {
 }
 
 int default_tile_bits(const sd_ctx *ctx, bool dbl) {
-    int K = ctx->tile_bits_opt > 0 ? ctx->tile_bits_opt : (dbl ? 12 : 13);
+    int K = ctx->tile_bits_opt > 0 ? ctx->tile_bits_opt
+            : ctx->tuned_k[dbl ? 1 : 0] > 0 ? ctx->tuned_k[dbl ? 1 : 0] : (dbl ? 12 : 13);
     return std::min(K, ctx->n);
 }
 
@@ -785,6 +787,7 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     ctx->grad_groups.clear();
     ctx->plan = std::move(p);
     ctx->tile_bits_opt = tb;
+    ctx->tuned_k[0] = ctx->tuned_k[1] = 0;
     ctx->jit_opt = jit;
     ctx->planned = true;
     // plan view
@@ -866,6 +869,85 @@ sd_status sd_prepare(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int 
     sd_status s = ensure_device(ctx);
     if (s != SD_OK || steps == 0) return s;
     return evolve_impl(ctx, nullptr, dtype == SD_C128, dt, steps, order, nullptr, false);
+}
+
+sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin, int kmax,
+                      int *best_k, double *times_ms) {
+    if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
+    if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");
+    if (dtype != SD_C64 && dtype != SD_C128) return fail(ctx, SD_EINVAL, "dtype must be SD_C64 or SD_C128");
+    if (order != 1 && order != 2) return fail(ctx, SD_EINVAL, "order must be 1 or 2");
+    if (steps < 1 || !std::isfinite(dt)) return fail(ctx, SD_EINVAL, "steps must be >= 1 and dt finite");
+    if (kmin < kRegBits + kLaneBits || kmax > 13 || kmin > kmax)
+        return fail(ctx, SD_EINVAL, "tile sizes must satisfy 9 <= kmin <= kmax <= 13");
+    const bool dbl = dtype == SD_C128;
+    const int d = dbl ? 1 : 0;
+    if (times_ms)
+        for (int k = kmin; k <= kmax; k++) times_ms[k - kmin] = 0.0;
+    if (best_k) *best_k = 0;
+    sd_status s = ensure_device(ctx);
+    if (s != SD_OK) return s;
+    if (use_onchip(ctx, dbl)) return SD_OK;   // nothing to tune: one launch runs every step
+    auto drop_programs = [&]() {
+        batch_purge(ctx);
+        for (auto &kv : ctx->programs) free_program(*kv.second);
+        ctx->programs.clear();
+    };
+    const size_t bytes = ((size_t)1 << ctx->n) * (dbl ? 16 : 8);
+    void *scratch = nullptr;
+    if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SD_ENOMEM, "no device memory for the autotuner's scratch state");
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int saved = ctx->tuned_k[d];
+    int best = 0;
+    double best_ms = 0.0;
+    s = SD_OK;
+    cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(scratch, 0, bytes, st);
+    if (ce != cudaSuccess) s = fail(ctx, SD_ECUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+    for (int K = kmin; K <= kmax && s == SD_OK; K++) {
+        if (K > ctx->n) break;
+        ctx->tuned_k[d] = K;
+        drop_programs();
+        // warm-up call of the timed shape (builds and compiles its programs)
+        sd_status r = evolve_impl(ctx, scratch, dbl, dt, steps, order, st);
+        if (r == SD_OK && cudaStreamSynchronize(st) != cudaSuccess) r = SD_ECUDA;
+        if (r != SD_OK) {
+            // a tile size the scheduler or the device cannot run is skipped
+            cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(e0, st);
+        r = evolve_impl(ctx, scratch, dbl, dt, steps, order, st);
+        cudaEventRecord(e1, st);
+        if (r != SD_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+            s = fail(ctx, SD_ECUDA, "autotune: timed run failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = (double)ms / (double)steps;
+        if (times_ms) times_ms[K - kmin] = per;
+        if (best == 0 || per < best_ms) {
+            best = K;
+            best_ms = per;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(scratch);
+    ctx->tuned_k[d] = s == SD_OK && best > 0 ? best : saved;
+    drop_programs();
+    if (s != SD_OK) return s;
+    if (best == 0) return fail(ctx, SD_EINVAL, "no tile size in the range could be scheduled");
+    if (best_k) *best_k = best;
+    return SD_OK;
 }
 
 sd_status sd_count_passes(sd_ctx *ctx, sd_dtype dtype, int order, int64_t steps, int64_t *out) {

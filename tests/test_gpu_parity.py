@@ -259,6 +259,31 @@ def test_batch_matches_individual(sd):
         assert np.linalg.norm(_host(t) - r) < 1e-4
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_autotune_tile_size(sd, dtype):
+    """The autotuner times tile sizes on its own scratch state, keeps the
+    fastest for the dtype, leaves the caller's state alone, and the tuned
+    path still matches the oracle."""
+    import torch
+    h = heisenberg_lattice(4, 4)
+    code = sd.C64 if dtype == "c64" else sd.C128
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    psi0 = basis_state(16, neel_index(4, 4))
+    t = _dev(psi0, dtype)
+    before = t.clone()
+    best, times = sim.autotune(code, 0.02, steps=4, order=1, kmin=10, kmax=13)
+    assert torch.equal(t, before)
+    assert best in times and min(times, key=times.get) == best
+    assert set(times) <= {10, 11, 12, 13} and all(v > 0 for v in times.values())
+    assert sim.schedule_stats(code, 1)["tile_bits"] == best
+    groups = P.greedy_partition(h.x, h.z)
+    ref = oracle.evolve(h, psi0, 0.02, 6, 1, groups)
+    sim.evolve(t, 0.02, 6, 1)
+    assert np.linalg.norm(_host(t) - ref) <= TOL[dtype]
+    with pytest.raises(sd.SDError):
+        sim.autotune(code, 0.02, kmin=8, kmax=13)
+
+
 def test_cuda_graph_capture(sd):
     """Once its programs are built, sd_evolve only launches kernels, and so
     does a prepared sd_evolve_batch: both are captured into a CUDA graph and
