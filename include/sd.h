@@ -70,7 +70,8 @@ typedef struct {
      * 2 = rule 1 plus qubits carrying only I/Y get S then H.  -1 = default (2). */
     int skip_rule;
     /* Tile size of the state-vector passes, log2 amplitudes per CTA tile:
-     * 0 = chosen by the autotuner, else 9..13. */
+     * 0 = default (13 for complex64, 12 for complex128, or what sd_autotune
+     * chose), else 9..13. */
     int tile_bits;
     /* Run-time specialisation of the tile passes (each pass compiled with
      * NVRTC for sm_103a, cached in memory and under $SD_JIT_CACHE or
@@ -78,7 +79,13 @@ typedef struct {
      * passes per program), 1 = always on the tile path, -1 = never.  Falls
      * back to the precompiled interpreter kernel if NVRTC is unavailable. */
     int jit;
-    int reserved[5];
+    /* Order of the greedy commuting partition (Sec. 2.3 asks only for a
+     * greedy method): 0 = first fit in input order (default); 1 = first fit
+     * in order of decreasing number of anticommuting terms (largest first);
+     * 2 = DSATUR colouring; 3 = first fit in order of decreasing |c_j| (the
+     * coefficients at sd_plan time).  1 and 2 take O(m^2) time. */
+    int grouping;
+    int reserved[4];
 } sd_plan_opts;
 
 /* Read-only view of a plan; pointers stay valid until the next sd_plan or

@@ -53,17 +53,86 @@ def commutes(x1: int, z1: int, x2: int, z2: int) -> bool:
 
 # ------------------------------------------------------------ partition
 
-def greedy_partition(x, z):
-    """First-fit greedy colouring: each term (in input order) joins the
-    lowest-index group all of whose members commute with it, otherwise it
-    opens a new group.  Returns a list of lists of term indices."""
+FIRST_FIT, LARGEST_FIRST, DSATUR, BY_MAGNITUDE = 0, 1, 2, 3
+
+
+def anticommutation_degrees(x, z):
+    """deg[j] = number of terms k != j with an odd symplectic product
+    |x_j & z_k| + |z_j & x_k| (the terms P_j anticommutes with)."""
+    x = np.asarray(x, dtype=np.uint64)
+    z = np.asarray(z, dtype=np.uint64)
+    deg = np.zeros(len(x), dtype=np.int64)
+    for j in range(len(x)):
+        odd = (np.bitwise_count(x[j] & z) + np.bitwise_count(z[j] & x)) & 1
+        deg[j] = int(odd.sum())
+    return deg
+
+
+def dsatur_partition(x, z):
+    """DSATUR colouring of the anticommutation graph: repeatedly take the
+    uncoloured term with the most distinct colours among its coloured
+    anticommuting terms (ties: larger degree, then lower index) and give it
+    the smallest colour none of them has.  Groups are the colour classes in
+    colour order, terms in input order."""
+    x = [int(v) for v in x]
+    z = [int(v) for v in z]
+    m = len(x)
+    deg = anticommutation_degrees(np.array(x, dtype=np.uint64), np.array(z, dtype=np.uint64))
+
+    def anti(a, b):
+        return (bin(x[a] & z[b]).count("1") + bin(z[a] & x[b]).count("1")) % 2 == 1
+
+    colour = [-1] * m
+    neigh = [set() for _ in range(m)]
+    groups = []
+    for _ in range(m):
+        v = max((u for u in range(m) if colour[u] < 0),
+                key=lambda u: (len(neigh[u]), deg[u], -u))
+        c = 0
+        while c in neigh[v]:
+            c += 1
+        colour[v] = c
+        if c == len(groups):
+            groups.append([])
+        groups[c].append(v)
+        for u in range(m):
+            if colour[u] < 0 and anti(u, v):
+                neigh[u].add(c)
+    return [sorted(g) for g in groups]
+
+
+def partition(x, z, grouping=FIRST_FIT, c=None):
+    """Commuting partition (Sec. 2.3 asks only for a greedy method) by
+    first fit in input order, first fit in order of decreasing degree
+    (largest first), DSATUR, or first fit in order of decreasing |c_j|.
+    Groups in order of creation, terms inside a group in input order."""
+    if grouping == FIRST_FIT:
+        return greedy_partition(x, z)
+    if grouping == DSATUR:
+        return dsatur_partition(x, z)
+    m = len(x)
+    if grouping == LARGEST_FIRST:
+        deg = anticommutation_degrees(x, z)
+        order = sorted(range(m), key=lambda j: -deg[j])           # stable: ties by index
+    elif grouping == BY_MAGNITUDE:
+        order = sorted(range(m), key=lambda j: -abs(float(c[j])))
+    else:
+        raise ValueError("grouping must be 0, 1, 2 or 3")
+    return [sorted(g) for g in greedy_partition(x, z, order)]
+
+
+def greedy_partition(x, z, order=None):
+    """First-fit greedy colouring: each term (in input order, or in `order`)
+    joins the lowest-index group all of whose members commute with it,
+    otherwise it opens a new group.  Returns a list of lists of term indices
+    (in the order they joined)."""
     x = np.asarray(x, dtype=np.uint64)
     z = np.asarray(z, dtype=np.uint64)
     groups: list[list[int]] = []
     gx: list[np.ndarray] = []
     gz: list[np.ndarray] = []
     gsize: list[int] = []
-    for j in range(len(x)):
+    for j in (range(len(x)) if order is None else order):
         xj, zj = x[j], z[j]
         placed = False
         for g in range(len(groups)):
@@ -402,8 +471,8 @@ class Plan:
         self.signs = signs
 
 
-def plan(n, x, z, skip_rule=SKIP_Y) -> Plan:
-    groups = greedy_partition(x, z)
+def plan(n, x, z, skip_rule=SKIP_Y, grouping=FIRST_FIT, c=None) -> Plan:
+    groups = partition(x, z, grouping, c)
     gates, masks, signs = [], [], []
     for g in groups:
         gt, mk, sg = synthesize_group(n, [x[j] for j in g], [z[j] for j in g], skip_rule)

@@ -116,9 +116,10 @@ class Simulator:
             pass
 
     # ------------------------------------------------------------ planning
-    def plan(self, skip_rule=-1, tile_bits=0, jit=0):
-        """Host planning.  jit: 0 automatic, 1 always, -1 never (see sd.h)."""
-        o = N.PlanOpts(skip_rule, tile_bits, jit)
+    def plan(self, skip_rule=-1, tile_bits=0, jit=0, grouping=0):
+        """Host planning.  jit: 0 automatic, 1 always, -1 never; grouping:
+        0 first fit, 1 largest first, 2 DSATUR, 3 by |c| (see sd.h)."""
+        o = N.PlanOpts(skip_rule, tile_bits, jit, grouping)
         self._check(self._lib.sd_plan(self._h, ctypes.byref(o)))
         return self
 

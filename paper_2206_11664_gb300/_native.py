@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "SD_OK", 1: "SD_EINVAL", 2: "SD_ENOMEM", 3: "SD_ECUDA", 4: "S
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("skip_rule", c_int), ("tile_bits", c_int), ("jit", c_int), ("reserved", c_int * 5)]
+    _fields_ = [("skip_rule", c_int), ("tile_bits", c_int), ("jit", c_int), ("grouping", c_int),
+                ("reserved", c_int * 4)]
 
 
 class PlanView(ctypes.Structure):

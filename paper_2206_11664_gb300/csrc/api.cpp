@@ -766,16 +766,18 @@ sd_status sd_set_coeffs(sd_ctx *ctx, const double *coeffs) {
 
 sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
-    int rule = 2, tb = 0, jit = 0;
+    int rule = 2, tb = 0, jit = 0, grouping = 0;
     if (opts) {
         rule = opts->skip_rule < 0 ? 2 : opts->skip_rule;
         tb = opts->tile_bits;
         jit = opts->jit;
+        grouping = opts->grouping;
         if (rule > 2) return fail(ctx, SD_EINVAL, "skip_rule must be -1, 0, 1 or 2");
         if (tb != 0 && (tb < 9 || tb > 13)) return fail(ctx, SD_EINVAL, "tile_bits must be 0 or 9..13");
+        if (grouping < 0 || grouping > 3) return fail(ctx, SD_EINVAL, "grouping must be 0, 1, 2 or 3");
     }
     Plan p;
-    std::string e = make_plan(ctx->n, ctx->m, ctx->x.data(), ctx->z.data(), rule, p);
+    std::string e = make_plan(ctx->n, ctx->m, ctx->x.data(), ctx->z.data(), rule, p, grouping, ctx->c.data());
     if (!e.empty()) return fail(ctx, SD_EINTERNAL, "planner: " + e);
     batch_purge(ctx);
     for (auto &kv : ctx->programs) free_program(*kv.second);

@@ -15,6 +15,7 @@
 //  * Skip rule: I/Z-only qubits untouched, I/X-only get H, and (rule 2)
 //    I/Y-only get S then H; these leave steps (i)-(iv).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "sd_internal.h"
@@ -309,37 +310,111 @@ std::string synthesize(int n, const std::vector<uint64_t> &xs, const std::vector
     return "";
 }
 
+// First fit in the given order: each term joins the first group (in order of
+// creation) all of whose members commute with it, else opens a new group.
+std::vector<std::vector<int64_t>> first_fit(const std::vector<int64_t> &order, const uint64_t *x,
+                                            const uint64_t *z) {
+    std::vector<std::vector<int64_t>> groups;
+    for (int64_t j : order) {
+        size_t g = 0;
+        for (; g < groups.size(); g++) {
+            bool ok = true;
+            for (int64_t k : groups[g])
+                if (anticommute(x[j], z[j], x[k], z[k])) { ok = false; break; }
+            if (ok) break;
+        }
+        if (g == groups.size()) groups.emplace_back();
+        groups[g].push_back(j);
+    }
+    return groups;
+}
+
+// Number of terms each term anticommutes with (its degree in the graph whose
+// colourings are the commuting partitions).
+std::vector<int64_t> degrees(int64_t m, const uint64_t *x, const uint64_t *z) {
+    std::vector<int64_t> d(m, 0);
+    for (int64_t a = 0; a < m; a++)
+        for (int64_t b = a + 1; b < m; b++)
+            if (anticommute(x[a], z[a], x[b], z[b])) {
+                d[a]++;
+                d[b]++;
+            }
+    return d;
+}
+
+// DSATUR: repeatedly colour the uncoloured term with the most distinct
+// colours among its coloured neighbours (ties: larger degree, then lower
+// index) with the smallest colour none of them has.
+std::vector<std::vector<int64_t>> dsatur(int64_t m, const uint64_t *x, const uint64_t *z) {
+    const std::vector<int64_t> deg = degrees(m, x, z);
+    std::vector<int64_t> colour(m, -1), sat(m, 0);
+    std::vector<std::vector<char>> seen(m);   // seen[u][c]: a neighbour of u has colour c
+    std::vector<std::vector<int64_t>> groups;
+    for (int64_t step = 0; step < m; step++) {
+        int64_t v = -1;
+        for (int64_t u = 0; u < m; u++) {
+            if (colour[u] >= 0) continue;
+            if (v < 0 || sat[u] > sat[v] || (sat[u] == sat[v] && deg[u] > deg[v])) v = u;
+        }
+        int64_t c = 0;
+        while (c < (int64_t)seen[v].size() && seen[v][c]) c++;
+        colour[v] = c;
+        if (c == (int64_t)groups.size()) groups.emplace_back();
+        groups[c].push_back(v);
+        for (int64_t u = 0; u < m; u++) {
+            if (colour[u] >= 0 || !anticommute(x[u], z[u], x[v], z[v])) continue;
+            if ((int64_t)seen[u].size() <= c) seen[u].resize(c + 1, 0);
+            if (!seen[u][c]) {
+                seen[u][c] = 1;
+                sat[u]++;
+            }
+        }
+    }
+    return groups;
+}
+
 }  // namespace
 
+std::vector<std::vector<int64_t>> partition_terms(int64_t m, const uint64_t *x, const uint64_t *z,
+                                                  const double *c, int grouping) {
+    std::vector<int64_t> order(m);
+    for (int64_t j = 0; j < m; j++) order[j] = j;
+    std::vector<std::vector<int64_t>> groups;
+    if (grouping == 1) {
+        const std::vector<int64_t> d = degrees(m, x, z);
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return d[a] > d[b]; });
+        groups = first_fit(order, x, z);
+    } else if (grouping == 2) {
+        groups = dsatur(m, x, z);
+    } else if (grouping == 3) {
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int64_t a, int64_t b) { return std::fabs(c[a]) > std::fabs(c[b]); });
+        groups = first_fit(order, x, z);
+    } else {
+        groups = first_fit(order, x, z);
+    }
+    for (auto &g : groups) std::sort(g.begin(), g.end());   // input order inside a group
+    return groups;
+}
+
 std::string make_plan(int n, int64_t m, const uint64_t *x, const uint64_t *z, int skip_rule,
-                      Plan &out) {
+                      Plan &out, int grouping, const double *c) {
     out = Plan{};
     out.n = n;
     out.skip_rule = skip_rule;
-    // Sec. 2.3: greedy (first-fit) partition into mutually commuting groups.
-    std::vector<std::vector<uint64_t>> gx, gz;
-    for (int64_t j = 0; j < m; j++) {
-        size_t g = 0;
-        for (; g < out.groups.size(); g++) {
-            bool ok = true;
-            const auto &X = gx[g];
-            const auto &Z = gz[g];
-            for (size_t k = 0; k < X.size(); k++)
-                if (anticommute(x[j], z[j], X[k], Z[k])) { ok = false; break; }
-            if (ok) break;
+    // Sec. 2.3: a greedy partition into mutually commuting groups (first fit
+    // in input order unless another colouring order is asked for).
+    const std::vector<std::vector<int64_t>> parts = partition_terms(m, x, z, c, grouping);
+    for (const auto &part : parts) {
+        out.groups.emplace_back();
+        std::vector<uint64_t> gx, gz;
+        for (int64_t j : part) {
+            out.groups.back().terms.push_back(j);
+            gx.push_back(x[j]);
+            gz.push_back(z[j]);
         }
-        if (g == out.groups.size()) {
-            out.groups.emplace_back();
-            gx.emplace_back();
-            gz.emplace_back();
-        }
-        out.groups[g].terms.push_back(j);
-        gx[g].push_back(x[j]);
-        gz[g].push_back(z[j]);
-    }
-    for (size_t g = 0; g < out.groups.size(); g++) {
-        std::string err = synthesize(n, gx[g], gz[g], skip_rule, out.groups[g]);
-        if (!err.empty()) return "group " + std::to_string(g) + ": " + err;
+        std::string err = synthesize(n, gx, gz, skip_rule, out.groups.back());
+        if (!err.empty()) return "group " + std::to_string(out.groups.size() - 1) + ": " + err;
     }
     return "";
 }

@@ -40,9 +40,16 @@ struct Plan {
 // Message returned by sd_last_error(NULL) on this thread.
 void set_last_error(const std::string &msg);
 
+// Commuting partition of the terms (Sec. 2.3: greedy).  grouping: 0 = first
+// fit in input order; 1 = first fit in order of decreasing anticommutation
+// degree (largest first); 2 = DSATUR; 3 = first fit in order of decreasing
+// |c_j|.  Groups in order of creation, terms inside a group in input order.
+std::vector<std::vector<int64_t>> partition_terms(int64_t m, const uint64_t *x, const uint64_t *z,
+                                                  const double *c, int grouping);
+
 // Returns an empty string on success, else the reason of failure.
 std::string make_plan(int n, int64_t m, const uint64_t *x, const uint64_t *z,
-                      int skip_rule, Plan &out);
+                      int skip_rule, Plan &out, int grouping = 0, const double *c = nullptr);
 
 // ------------------------------------------------------------ flat ops
 

@@ -43,9 +43,11 @@ def _rand_state(rng, n):
     return v / np.linalg.norm(v)
 
 
-def _check(sd, h, psi0, dt_, steps, order, dtype, skip_rule=-1, tile_bits=0, pauli=False, jit=0):
-    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(skip_rule=skip_rule, tile_bits=tile_bits, jit=jit)
-    groups = P.greedy_partition(h.x, h.z)
+def _check(sd, h, psi0, dt_, steps, order, dtype, skip_rule=-1, tile_bits=0, pauli=False, jit=0,
+           grouping=0):
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(skip_rule=skip_rule, tile_bits=tile_bits, jit=jit,
+                                                grouping=grouping)
+    groups = P.partition(h.x, h.z, grouping, h.c)
     ref = oracle.evolve(h, psi0, dt_, steps, order, groups)
     t = _dev(psi0, dtype)
     if pauli:
@@ -135,6 +137,16 @@ def test_tile_jw_like(sd):
     psi0 = basis_state(15, (1 << 7) - 1)
     _check(sd, h, psi0, 0.05, 3, 2, "c128")
     _check(sd, h, psi0, 0.05, 3, 2, "c64")
+
+
+@pytest.mark.parametrize("grouping", [1, 2, 3])
+def test_grouping_variants(sd, grouping):
+    """Largest-first, DSATUR and |c|-ordered partitions evolve like the
+    oracle does with the same groups (tile path, both orders)."""
+    rng = np.random.default_rng(80 + grouping)
+    h = random_klocal(15, 80, rng, weights=(2, 3, 4))
+    _check(sd, h, _rand_state(rng, 15), 0.05, 2, 1, "c128", grouping=grouping)
+    _check(sd, h, _rand_state(rng, 15), 0.05, 2, 2, "c64", grouping=grouping)
 
 
 def test_paper_models(sd):

@@ -156,3 +156,21 @@ def test_count_passes_blocks(sd):
     assert small.count_passes(sd.C128, 1, 100) == 0
     with pytest.raises(sd.SDError):
         sim.count_passes(sd.C64, 3, 1)
+
+
+def test_grouping_variants_match_oracle(sd):
+    """The four partition orders of the product planner give the oracle
+    planner's groups exactly (and the plans diagonalise them)."""
+    rng = np.random.default_rng(72)
+    cases = [random_klocal(n, m, rng, weights=(1, 2, 3)) for n, m in ((8, 60), (12, 200), (16, 300))]
+    cases.append(jw_like(n=12, m=300, rng=rng))
+    for h in cases:
+        for g in range(4):
+            ref = P.partition(h.x, h.z, g, h.c)
+            sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(grouping=g)
+            v = sim.plan_view()
+            got = [v["group_terms"][v["group_offsets"][i]:v["group_offsets"][i + 1]].tolist()
+                   for i in range(v["n_groups"])]
+            assert got == ref, (h.n, h.m, g)
+    with pytest.raises(sd.SDError):
+        sd.Simulator(cases[0].n, cases[0].x, cases[0].z, cases[0].c).plan(grouping=4)

@@ -271,3 +271,59 @@ def test_cnot_layer_matrix_is_the_cnot_permutation():
                 if (img >> q) & 1:
                     back ^= Ainv[q]
             assert back == v
+
+
+# ---------------------------------------------------------------- grouping variants
+
+def _valid_partition(x, z, groups):
+    seen = sorted(j for g in groups for j in g)
+    assert seen == list(range(len(x)))
+    for g in groups:
+        for a in g:
+            for b in g:
+                assert (bin(int(x[a]) & int(z[b])).count("1") + bin(int(z[a]) & int(x[b])).count("1")) % 2 == 0
+
+
+def _crown(k):
+    """u_i = Z_i and v_j = X on every qubit but j (k qubits): u_i and v_j
+    anticommute exactly when i != j, the u commute, the v commute (a crown
+    graph, bipartite), listed u_1, v_1, u_2, v_2, ..."""
+    full = (1 << k) - 1
+    x, z = [], []
+    for i in range(k):
+        x += [0, full ^ (1 << i)]
+        z += [1 << i, 0]
+    return np.array(x, dtype=np.uint64), np.array(z, dtype=np.uint64)
+
+
+def test_grouping_variants_are_partitions():
+    rng = np.random.default_rng(71)
+    from workloads import random_klocal
+    for n, m in ((6, 40), (10, 120)):
+        h = random_klocal(n, m, rng, weights=(1, 2, 3))
+        for g in range(4):
+            _valid_partition(h.x, h.z, P.partition(h.x, h.z, g, h.c))
+
+
+def test_dsatur_is_exact_on_a_crown_graph():
+    """On a bipartite anticommutation graph DSATUR needs 2 groups; first fit
+    in this input order needs k, and so does largest first (all degrees equal)."""
+    k = 6
+    x, z = _crown(k)
+    assert len(P.partition(x, z, P.DSATUR)) == 2
+    assert len(P.partition(x, z, P.FIRST_FIT)) == k
+    assert len(P.partition(x, z, P.LARGEST_FIRST)) == k
+    assert P.anticommutation_degrees(x, z).tolist() == [k - 1] * (2 * k)
+
+
+def test_largest_first_and_magnitude_orders():
+    # Z_0, Z_1, Z_2 commute; X_0 X_1 X_2 anticommutes with each of them
+    x = np.array([0, 0, 0, 7], dtype=np.uint64)
+    z = np.array([1, 2, 4, 0], dtype=np.uint64)
+    assert P.anticommutation_degrees(x, z).tolist() == [1, 1, 1, 3]
+    assert P.partition(x, z, P.FIRST_FIT) == [[0, 1, 2], [3]]
+    assert P.partition(x, z, P.LARGEST_FIRST) == [[3], [0, 1, 2]]
+    c = np.array([0.1, 0.2, 0.3, 0.05])
+    assert P.partition(x, z, P.BY_MAGNITUDE, c) == [[0, 1, 2], [3]]
+    c2 = np.array([0.1, 0.2, 0.3, 5.0])
+    assert P.partition(x, z, P.BY_MAGNITUDE, c2) == [[3], [0, 1, 2]]
