@@ -416,6 +416,21 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
         int h_count = 0;
         int diag_op_index = -1;
 
+        // Another pass follows if a pending gate acts on a qubit outside this
+        // tile.  Then, once this pass has applied a group exponential, the
+        // gates that follow it on the low (coalescing) qubits are left to the
+        // next pass, which holds those qubits too: exponential passes are
+        // bound by instruction issue, the passes between them by memory.
+        bool more_passes = false;
+        for (int j = first; j < N && !more_passes; j++) {
+            if (done[j] >= 0) continue;
+            const FlatOp &op = circ.ops[j];
+            if (is_1q(op.kind)) more_passes = pos_of[op.q] < 0;
+            else if (op.kind == OK_CNOT) more_passes = pos_of[op.q2] < 0 || pos_of[op.q] < 0;
+        }
+        auto deferred = [&](const FlatOp &op) {
+            return more_passes && diag_op_index >= 0 && is_1q(op.kind) && op.q < c;
+        };
         int nr = 0;
         for (;;) {
             bool is_load = nr == 0;
@@ -430,7 +445,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                     if (done[j] >= 0) continue;
                     const FlatOp &op = circ.ops[j];
                     if (is_1q(op.kind) && op.q == tq[p]) {
-                        bool ready = true;
+                        bool ready = !deferred(op);
                         for (int pr : preds[j])
                             if (done[pr] < 0) { ready = false; break; }
                         if (ready) best = j;
@@ -493,7 +508,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
                     int slot = -1;
                     if (is_1q(op.kind)) {
                         int p = pos_of[op.q];
-                        if (p < 0) continue;
+                        if (p < 0 || deferred(op)) continue;
                         for (int i = 0; i < 4; i++)
                             if (R.reg_pos[i] == p) slot = i;
                         if (slot < 0) continue;
