@@ -149,6 +149,16 @@ sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_st
  * SD_EINVAL / SD_ENOPLAN as for sd_evolve. */
 sd_status sd_prepare(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order);
 
+/* sd_evolve on a state held in host memory: the 2^n amplitudes of
+ * `dtype` at host_state (page-locked: cudaHostAlloc, cudaHostRegister or
+ * torch pin_memory; pageable memory gives SD_EINVAL) are copied to d_work
+ * (a caller-owned device buffer of the same size), evolved there, and copied
+ * back, the copies done by kernels that read and write the host buffer
+ * through its mapped address.  Asynchronous on the stream: host_state holds
+ * the result once the stream has reached this point. */
+sd_status sd_evolve_host(sd_ctx *ctx, void *host_state, void *d_work, sd_dtype dtype, double dt,
+                         int64_t steps, int order, void *cuda_stream);
+
 /* Tile-size autotuner.  For each tile size K = kmin..kmax (9 <= kmin <=
  * kmax <= 13; a tile is 2^K amplitudes staged in one block's shared memory),
  * runs sd_evolve(., dt, steps, order) once to build and compile its programs

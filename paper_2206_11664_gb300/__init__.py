@@ -189,6 +189,18 @@ class Simulator:
                                         _stream(stream)))
         return state
 
+    def evolve_host(self, host_state, work, dt, steps, order=1, stream=None):
+        """End to end: copy the pinned host tensor `host_state` into the device
+        tensor `work`, evolve it there, copy it back (one asynchronous call)."""
+        if not host_state.is_pinned():
+            raise ValueError("host_state must be pinned (pin_memory())")
+        if host_state.dtype != work.dtype or host_state.numel() != work.numel():
+            raise ValueError("work must match host_state in dtype and size")
+        self._check(self._lib.sd_evolve_host(self._h, ctypes.c_void_p(host_state.data_ptr()),
+                                             ctypes.c_void_p(work.data_ptr()), _dtype_of(work, self.n),
+                                             float(dt), int(steps), int(order), _stream(stream)))
+        return host_state
+
     def evolve_pauli(self, state, dt, steps, order=1, stream=None):
         """Baseline: one state pass per term (same product, ungrouped)."""
         self._check(self._lib.sd_evolve_pauli(self._h, ctypes.c_void_p(state.data_ptr()),

@@ -952,6 +952,27 @@ sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int
     return SD_OK;
 }
 
+sd_status sd_evolve_host(sd_ctx *ctx, void *host_state, void *d_work, sd_dtype dtype, double dt,
+                         int64_t steps, int order, void *cuda_stream) {
+    sd_status s = check_state_args(ctx, d_work, dtype, order);
+    if (s != SD_OK) return s;
+    if (!host_state) return fail(ctx, SD_EINVAL, "null host state");
+    if (steps < 0 || !std::isfinite(dt)) return fail(ctx, SD_EINVAL, "invalid steps or dt");
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, host_state) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return fail(ctx, SD_EINVAL, "host state must be page-locked host memory (cudaHostAlloc, cudaHostRegister)");
+    }
+    const bool dbl = dtype == SD_C128;
+    const size_t bytes = ((size_t)1 << ctx->n) * (dbl ? 16 : 8);
+    void *hp = at.devicePointer ? at.devicePointer : host_state;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    CK(launch_copy16(hp, d_work, bytes, ctx->num_sms, st));
+    if (steps > 0 && (s = evolve_impl(ctx, d_work, dbl, dt, steps, order, st)) != SD_OK) return s;
+    CK(launch_copy16(d_work, hp, bytes, ctx->num_sms, st));
+    return SD_OK;
+}
+
 sd_status sd_count_passes(sd_ctx *ctx, sd_dtype dtype, int order, int64_t steps, int64_t *out) {
     if (!ctx || !out) return fail(nullptr, SD_EINVAL, "null argument");
     if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");

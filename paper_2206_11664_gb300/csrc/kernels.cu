@@ -901,6 +901,23 @@ cudaError_t launch_expect_pauli(bool dbl, const void *psi, int n, uint64_t x, ui
     return cudaGetLastError();
 }
 
+// 16-byte grid-stride copy; either side may be page-locked host memory
+// addressed through its mapped (unified) address, so that the SMs move the
+// state over the host link.
+__global__ void copy16_kernel(const int4 *__restrict__ src, int4 *__restrict__ dst, int64_t n16) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = src[i];
+}
+
+cudaError_t launch_copy16(const void *src, void *dst, size_t bytes, int num_sms, cudaStream_t st) {
+    const int64_t n16 = (int64_t)(bytes / 16);
+    if (n16 == 0) return cudaSuccess;
+    int64_t grid = (int64_t)num_sms * 4;
+    if (grid > (n16 + 511) / 512) grid = (n16 + 511) / 512;
+    copy16_kernel<<<(unsigned)grid, 512, 0, st>>>((const int4 *)src, (int4 *)dst, n16);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const double *partial, int64_t count, double *out, int accumulate,
                           cudaStream_t st) {
     reduce_kernel<<<1, 1024, 0, st>>>(partial, count, out, accumulate);

@@ -90,6 +90,7 @@ cudaError_t launch_expect_diag(bool dbl, const void *psi, int n, const uint64_t 
 cudaError_t launch_expect_pauli(bool dbl, const void *psi, int n, uint64_t x, uint64_t z,
                                 double coef, double *partial, int blocks, cudaStream_t st);
 // out[0] (+)= sum of partial[0..count) in fixed order.
+cudaError_t launch_copy16(const void *src, void *dst, size_t bytes, int num_sms, cudaStream_t st);
 cudaError_t launch_reduce(const double *partial, int64_t count, double *out, int accumulate,
                           cudaStream_t st);
 

@@ -5,6 +5,8 @@ Tolerances: ||psi_gpu - psi_oracle||_2 <= 1e-10 for complex128 states and
 oracle applies one rotation at a time in group order; the GPU applies whole
 groups through their Clifford frames, so agreement is up to rounding only.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -340,6 +342,30 @@ def test_cuda_graph_capture(sd):
     with pytest.raises(sd.SDError):
         with torch.cuda.graph(g2):
             sd.evolve_batch(sims, other, 0.03, 3, 2)
+
+
+def test_evolve_host(sd):
+    """sd_evolve_host: pinned host state in, the same result as sd_evolve on
+    a device copy out; pageable host memory is refused."""
+    import torch
+    rng = np.random.default_rng(66)
+    h = heisenberg_lattice(4, 4)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    psi0 = _rand_state(rng, h.n)
+    ref = _dev(psi0, "c64")
+    sim.evolve(ref, 0.02, 5, 1)
+    host = torch.from_numpy(psi0.astype(np.complex64)).pin_memory()
+    work = torch.empty_like(ref)
+    sim.evolve_host(host, work, 0.02, 5, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(host, ref.cpu())
+    pageable = torch.from_numpy(psi0.astype(np.complex64))
+    with pytest.raises(ValueError):
+        sim.evolve_host(pageable, work, 0.02, 1, 1)
+    N = sd._native
+    st = sim._lib.sd_evolve_host(sim._h, ctypes.c_void_p(pageable.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                 N.SD_C64, 0.02, 1, 1, None)
+    assert st == N.SD_EINVAL
 
 
 def test_invalid_state_rejected(sd):
