@@ -151,6 +151,39 @@ def test_grouping_variants(sd, grouping):
     _check(sd, h, _rand_state(rng, 15), 0.05, 2, 2, "c64", grouping=grouping)
 
 
+@pytest.mark.parametrize("jit", [-1, 1])
+def test_large_diagonal_groups(sd, jit):
+    """Groups of Z-strings only (no Clifford): 1500 terms, whose terms the
+    passes keep in shared memory, and 5000 terms, read from global memory
+    instead; many terms share a slot (class and fixed-position mask)."""
+    rng = np.random.default_rng(90)
+    n = 16
+    for m in (1500, 5000):
+        z = rng.integers(1, 1 << n, size=m, dtype=np.uint64) & rng.integers(0, 1 << n, size=m, dtype=np.uint64)
+        z[z == 0] = 1
+        from workloads import Hamiltonian
+        h = Hamiltonian(n, np.zeros(m, dtype=np.uint64), z, rng.uniform(-1, 1, size=m))
+        for dtype in ("c128", "c64"):
+            _check(sd, h, _rand_state(rng, n), 0.05, 2, 1, dtype, jit=jit)
+
+
+def test_trivial_calls(sd):
+    """steps = 0 leaves the state alone; dt = 0 is the identity within the
+    tolerance; a Hamiltonian of single-qubit X terms on the tile path."""
+    import torch
+    h = heisenberg_lattice(4, 4)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    rng = np.random.default_rng(91)
+    psi0 = _rand_state(rng, h.n)
+    t = _dev(psi0, "c128")
+    sim.evolve(t, 0.02, 0, 1)
+    assert torch.equal(t, _dev(psi0, "c128"))
+    sim.evolve(t, 0.0, 3, 2)
+    assert np.linalg.norm(_host(t) - psi0) <= TOL["c128"]
+    hx = from_strings(["I" * q + "X" + "I" * (15 - q) for q in range(16)], rng.uniform(-1, 1, 16))
+    _check(sd, hx, _rand_state(rng, 16), 0.1, 3, 1, "c64")
+
+
 def test_paper_models(sd):
     """The paper's two experiment Hamiltonians (Sec. 4): the fully connected
     transverse-field Ising model (2 groups, 10 steps on the tile path, both
