@@ -45,6 +45,8 @@ def parse():
                              "tfim_fc", "syk", "sweep"],
                     help="heisenberg30 is the benchmark line; the others measure the remaining "
                          "configurations and print their own line")
+    ap.add_argument("--tile-bits", dest="tile_bits", type=int, default=0,
+                    help="tile size for the batch workload (0 = default)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the tile size by timing K = 11..13 first (sd_autotune)")
     ap.add_argument("--state", default="c64", choices=["c64", "c128"],

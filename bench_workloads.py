@@ -93,7 +93,7 @@ def batch(args):
     inst = batch_instances(64)
     sims, states = [], []
     for h, fac in inst:
-        sims.append(sd.Simulator(h.n, h.x, h.z, h.c).plan())
+        sims.append(sd.Simulator(h.n, h.x, h.z, h.c).plan(tile_bits=getattr(args, "tile_bits", 0)))
         states.append(torch.from_numpy(product_state(fac, np.complex64)).cuda())
     setup = time.perf_counter() - t0
     k = max(2, args.steps // 10)
@@ -102,7 +102,8 @@ def batch(args):
     nbytes = sum(s.schedule_stats(sd.C64, 2)["passes_per_step"] * 2 * (1 << s.n) * 8 for s in sims)
     _line("batch instance-steps/s (64 instances, second order)", 64 * k / t, "instance-steps/s",
           {"workload": "random_klocal_batch_64", "n_range": [min(s.n for s in sims), max(s.n for s in sims)],
-           "terms": 2000, "dt": 0.005, "order": 2, "state": "complex64"},
+           "terms": 2000, "dt": 0.005, "order": 2, "state": "complex64",
+           "tile_bits": getattr(args, "tile_bits", 0) or "default"},
           steps=k, ms_per_batch_step=1e3 * t / k, achieved_gbs=nbytes * k / t / 1e9,
           host_setup_s=setup)
 

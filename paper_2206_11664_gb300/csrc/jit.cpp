@@ -331,7 +331,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                         o << "        { const uint64_t v = (uint64_t)TCQ[" << i << "]; acc += (__popcll(xo & "
                           << hex64(S.term_mo[t]) << ") & 1) ? 0ull - v : v; }\n";
                     }
-                    o << "        ST[" << j << "].q = acc; }\n";
+                    o << "        ST[" << j << "].q = acc; ST[" << j << "].ml = " << hex32(sl.ml) << "; }\n";
                 }
             } else {
                 o << "      stage_slots(xo, kp.slots, " << R.slot_begin << ", " << R.slot_count
