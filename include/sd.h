@@ -31,10 +31,14 @@
  * every device work buffer it allocates; the caller owns state buffers and
  * host output arrays.  No call frees or reallocates caller memory.
  *
- * Ordering.  sd_evolve, sd_evolve_observe, sd_evolve_pauli and
- * sd_evolve_batch are asynchronous on the given CUDA stream (NULL = legacy
- * default stream); sd_expect and sd_grad synchronise the stream to return
- * host values.
+ * Ordering.  sd_evolve, sd_evolve_observe, sd_evolve_pauli, sd_evolve_host
+ * and sd_evolve_batch are asynchronous on the given CUDA stream (NULL =
+ * legacy default stream); sd_expect and sd_grad synchronise the stream to
+ * return host values.  sd_prepare, sd_prepare_batch and sd_autotune are
+ * synchronous; sd_plan, sd_get_plan, sd_get_schedule and sd_count_passes are
+ * host only.  A call whose programs are built (by sd_prepare or an earlier
+ * identical call) only launches kernels and may be captured into a CUDA
+ * graph.
  */
 #ifndef SD_H
 #define SD_H
