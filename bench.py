@@ -313,6 +313,16 @@ def main():
            "gpu_launches": launches,
            "clocks": ck,
            "norm_error": norm_err}
+    if not args.no_extras and args.state == "c64":
+        # accuracy of the timed result: the same warmup + steps in complex128
+        # (the complex128 path matches the oracle to 1e-10 in the parity tests)
+        ref = fresh(torch.complex128)
+        sim.evolve(ref, DT, args.warmup, 1)
+        sim.evolve(ref, DT, args.steps, 1)
+        diff = float(torch.linalg.vector_norm(state.to(torch.complex128) - ref).item())
+        out["accuracy"] = {"l2_vs_complex128": diff, "steps": args.warmup + args.steps,
+                           "tolerance": 1e-4}
+        del ref
     del state
     torch.cuda.empty_cache()
 
