@@ -177,6 +177,16 @@ sd_status sd_evolve_host(sd_ctx *ctx, void *host_state, void *d_work, sd_dtype d
 sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin,
                       int kmax, int *best_k, double *times_ms);
 
+/* Compiles, host only (no GPU, no CUDA driver needed: NVRTC only), the
+ * kernels that sd_evolve(ctx, ., dtype, ., steps, order, .) would compile
+ * at run time, into the on-disk kernel cache ($SD_JIT_CACHE, else
+ * $XDG_CACHE_HOME/sd_jit or ~/.cache/sd_jit) that later sd_evolve calls on
+ * a GPU read.  The kernels do not depend on dt.  *compiled (may be NULL)
+ * receives the number of NVRTC programs compiled (0 when all were cached,
+ * or when nothing is compiled at run time for this call).  SD_EINVAL if
+ * NVRTC is unavailable. */
+sd_status sd_precompile(sd_ctx *ctx, sd_dtype dtype, int64_t steps, int order, int64_t *compiled);
+
 /* Number of tile-pass kernels sd_evolve(ctx, ., dtype, ., steps, order, .)
  * launches; each reads and writes the state once.  0 when the state stays
  * on chip (one launch then runs every step).  A call of several steps merges

@@ -175,6 +175,14 @@ class Simulator:
                                           ctypes.byref(best), times.ctypes.data_as(N.P_dbl)))
         return best.value, {kmin + i: float(t) for i, t in enumerate(times) if t > 0}
 
+    def precompile(self, dtype, steps, order=1):
+        """Compile (host only, NVRTC) the kernels evolve(., dt, steps, order)
+        compiles at run time into the on-disk cache; returns the number of
+        NVRTC programs compiled."""
+        out = ctypes.c_int64(0)
+        self._check(self._lib.sd_precompile(self._h, dtype, int(steps), int(order), ctypes.byref(out)))
+        return out.value
+
     def count_passes(self, dtype=C64, order=1, steps=1):
         """Tile-pass launches evolve() makes for `steps` steps (0 on chip)."""
         out = ctypes.c_int64(0)

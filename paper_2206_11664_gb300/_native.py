@@ -49,6 +49,7 @@ SIGNATURES = {
     "sd_prepare": (c_int, [c_vp, c_int, c_dbl, c_i64, c_int]),
     "sd_autotune": (c_int, [c_vp, c_int, c_dbl, c_i64, c_int, c_int, c_int, ctypes.POINTER(c_int), P_dbl]),
     "sd_evolve_host": (c_int, [c_vp, c_vp, c_vp, c_int, c_dbl, c_i64, c_int, c_vp]),
+    "sd_precompile": (c_int, [c_vp, c_int, c_i64, c_int, ctypes.POINTER(c_i64)]),
     "sd_count_passes": (c_int, [c_vp, c_int, c_int, c_i64, ctypes.POINTER(c_i64)]),
     "sd_evolve": (c_int, [c_vp, c_vp, c_int, c_dbl, c_i64, c_int, c_vp]),
     "sd_evolve_observe": (c_int, [c_vp, c_vp, c_int, c_dbl, c_i64, c_int, c_i64, P_u64, P_u64,

@@ -223,6 +223,18 @@ sd_status schedule_for(sd_ctx *ctx, const Circuit &circ, bool dbl, Schedule &S) 
     }
 }
 
+// Whether a program of `passes` tile passes is compiled at run time: always
+// with jit = 1 (or SD_JIT=1), never with jit = -1 (or SD_JIT=0), else for
+// states of 20+ qubits and at most kJitMaxPasses passes.  One-shot programs
+// (the half steps that open and close a second-order evolution,
+// allow_jit = false) are not worth a compilation unless it is forced.
+bool jit_wanted(const sd_ctx *ctx, bool allow_jit, int64_t passes) {
+    int mode = ctx->jit_opt;
+    if (const char *e = getenv("SD_JIT")) mode = atoi(e) > 0 ? 1 : (e[0] == '0' ? -1 : mode);
+    if (passes <= 0) return false;
+    return mode > 0 || (mode == 0 && allow_jit && ctx->n >= 20 && passes <= kJitMaxPasses);
+}
+
 // Build and upload a program for a circuit.
 sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &P,
                         bool allow_jit = true) {
@@ -286,12 +298,7 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
     P.passes = (int64_t)S.passes.size();
     P.rounds = (int64_t)S.rounds.size();
     P.diag_passes = S.diag_passes;
-    int mode = ctx->jit_opt;
-    if (const char *e = getenv("SD_JIT")) mode = atoi(e) > 0 ? 1 : (e[0] == '0' ? -1 : mode);
-    // one-shot programs (the half steps that open and close a second-order
-    // evolution) are not worth a compilation unless specialisation is forced
-    const bool want = mode > 0 || (mode == 0 && allow_jit && n >= 20 && P.passes <= kJitMaxPasses);
-    if (want && P.passes > 0) {
+    if (jit_wanted(ctx, allow_jit, P.passes)) {
         std::string why = jit_build(S, n, dbl, P.jit);
         if (!why.empty()) {
             P.jit = JitProgram{};
@@ -970,6 +977,47 @@ sd_status sd_evolve_host(sd_ctx *ctx, void *host_state, void *d_work, sd_dtype d
     CK(launch_copy16(hp, d_work, bytes, ctx->num_sms, st));
     if (steps > 0 && (s = evolve_impl(ctx, d_work, dbl, dt, steps, order, st)) != SD_OK) return s;
     CK(launch_copy16(d_work, hp, bytes, ctx->num_sms, st));
+    return SD_OK;
+}
+
+sd_status sd_precompile(sd_ctx *ctx, sd_dtype dtype, int64_t steps, int order, int64_t *compiled) {
+    if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
+    if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");
+    if (dtype != SD_C64 && dtype != SD_C128) return fail(ctx, SD_EINVAL, "dtype must be SD_C64 or SD_C128");
+    if (order != 1 && order != 2) return fail(ctx, SD_EINVAL, "order must be 1 or 2");
+    if (steps < 0) return fail(ctx, SD_EINVAL, "steps must be >= 0");
+    if (compiled) *compiled = 0;
+    const bool dbl = dtype == SD_C128;
+    if (steps == 0 || use_onchip(ctx, dbl)) return SD_OK;
+    const int G = (int)ctx->plan.groups.size();
+    // the segments sd_evolve would run: (kind, repetitions in one program)
+    std::vector<std::pair<int, int>> segs;
+    int64_t one = 0;
+    sd_status s;
+    const int base = (order == 1 || G == 1 || steps == 1) ? 0 : 2;
+    const int64_t count = base == 0 ? steps : steps - 1;
+    if (base == 2) {
+        segs.push_back({1, 1});
+        segs.push_back({3, 1});
+    }
+    if ((s = segment_passes(ctx, dbl, order, base, 1, one)) != SD_OK) return s;
+    const int M = block_steps(one);
+    if (count > 0 && (count % M != 0 || M == 1)) segs.push_back({base, 1});
+    if (M > 1 && count >= M) segs.push_back({4, M});
+    int64_t total = 0;
+    for (auto &sg : segs) {
+        Circuit c = segment_circuit(ctx, order, sg.first, 0.01, sg.second);
+        canonicalize_1q(c, ctx->n);
+        Schedule S;
+        if ((s = schedule_for(ctx, c, dbl, S)) != SD_OK) return s;
+        const bool allow = sg.first == 0 || sg.first == 2 || sg.first == 4;
+        if (!jit_wanted(ctx, allow, (int64_t)S.passes.size())) continue;
+        int done = 0;
+        const std::string e = jit_precompile(S, ctx->n, dbl, &done);
+        if (!e.empty()) return fail(ctx, SD_EINVAL, "run-time compilation: " + e);
+        total += done;
+    }
+    if (compiled) *compiled = total;
     return SD_OK;
 }
 

@@ -193,6 +193,10 @@ void emit_mono_fx(std::ostringstream &o, int I, int PA, int XX, int *kph) {
     }
 }
 
+// Limits of the straight-line code emitted for a round's group exponentials.
+constexpr int kInlineTerms = 384;   // terms staged per round
+constexpr int kInlineSlots = 192;   // slots per round / per exponential
+
 // Whether class u of a group exponential has any term on the tile.
 bool diag_class_used(const DevDiag &d, int u) {
     return d.off[u + 1] > d.off[u] || d.zs[u] >= 0 || (u == 0 && d.cst >= 0);
@@ -320,7 +324,15 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         if (r == 0) o << "      cp_async_wait_all();\n";
         o << "      __syncthreads();\n";
         if (R.n_diag > 0) {
-            if (P.term_cache) {
+            // Straight-line code only for rounds of modest size: longer code
+            // compiles slowly and gains nothing once the work is spread out.
+            int round_terms = 0;
+            for (int j = 0; j < R.slot_count; j++) round_terms += S.slots[R.slot_begin + j].tn;
+            const bool inline_stage = round_terms <= kInlineTerms && R.slot_count <= kInlineSlots;
+            if (P.term_cache && !inline_stage) {
+                o << "      stage_slots(xo, kp.slots, " << R.slot_begin << ", " << R.slot_count
+                  << ", TCM, TCQ, " << P.term_begin << ", ST, tid, NT);\n";
+            } else if (P.term_cache) {
                 // one thread per slot, spread over the warps; masks inline, angles from the cache
                 for (int j = 0; j < R.slot_count; j++) {
                     const DevSlot &sl = S.slots[R.slot_begin + j];
@@ -343,7 +355,10 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                       << R.cst_begin[cc] << ", " << R.cst_count[cc] << ", lane); if (lane == 0) CST[" << cc << "] = v; }\n";
             o << "      __syncthreads();\n";
             // class totals, one thread each, spread over the warps
-            for (int k = 0; k < R.n_diag; k++) {
+            if (!inline_stage)
+                o << "      stage_totals(kp, " << R.diag_begin << ", " << R.n_diag << ", ST, CST, "
+                  << hex64(dbl_state ? 0 : (1ull << 31)) << ", TQ, tid, NT);\n";
+            for (int k = 0; k < R.n_diag && inline_stage; k++) {
                 const DevDiag &d = S.diags[R.diag_begin + k];
                 for (int u = 0; u < 16; u++) {
                     if (!diag_class_used(d, u)) continue;
@@ -428,7 +443,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                 const DevDiag &d = S.diags[op.arg];
                 const double sc = (op.pad && !table_scaled) ? P.scale : 1.0;
                 o << "      { uint64_t G[16];\n";
-                const bool unrolled = d.off[16] <= 512;
+                const bool unrolled = d.off[16] <= kInlineSlots;
                 for (int u = 0; u < 16; u++) {
                     if (!diag_class_used(d, u)) {
                         o << "        G[" << u << "] = 0ull;\n";
@@ -608,35 +623,40 @@ std::string jit_compile_check(const std::string &src) {
     return compile_cubin(src, cubin);
 }
 
-// Passes are compiled in chunks (one NVRTC program each, on a pool of host
-// threads); each chunk's cubin is cached in memory and on disk by the hash of
-// its source.
-std::string jit_build(const Schedule &S, int n, bool dbl_state, JitProgram &out) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    init_locked();
-    if (!(g_nvrtc.ok && g_drv.ok)) return g_why;
+namespace {
+
+constexpr int kChunk = 12;   // passes per NVRTC program
+
+// Sources, cache keys and cubins of S's pass chunks: cubins come from the
+// in-memory module table (left empty, mods[c] set), the disk cache, or NVRTC
+// (compiled on a pool of host threads and written to the disk cache).
+// Called with g_mu held.
+std::string chunk_cubins(const Schedule &S, int n, bool dbl_state, std::vector<std::string> &key,
+                         std::vector<std::string> &cubin, std::vector<CUmodule> *mods, int *compiled) {
     const int P = (int)S.passes.size();
-    const int chunk = 12;
-    const int nchunks = (P + chunk - 1) / chunk;
+    const int nchunks = (P + kChunk - 1) / kChunk;
     int maj = 0, min = 0;
     g_nvrtc.version(&maj, &min);
-    std::vector<std::string> code(nchunks), key(nchunks), cubin(nchunks), err(nchunks);
-    std::vector<CUmodule> mods(nchunks, nullptr);
+    std::vector<std::string> code(nchunks), err(nchunks);
+    key.assign(nchunks, "");
+    cubin.assign(nchunks, "");
+    if (mods) mods->assign(nchunks, nullptr);
     const std::string dir = cache_dir();
     std::vector<int> todo;
     for (int c = 0; c < nchunks; c++) {
-        code[c] = source_range(S, n, dbl_state, c * chunk, std::min(P, (c + 1) * chunk));
+        code[c] = source_range(S, n, dbl_state, c * kChunk, std::min(P, (c + 1) * kChunk));
         key[c] = std::to_string(std::hash<std::string>{}(code[c])) + "_" + std::to_string(code[c].size()) +
                  "_nvrtc" + std::to_string(maj) + "." + std::to_string(min);
         auto it = g_modules.find(key[c]);
-        if (it != g_modules.end()) {
-            mods[c] = it->second;
+        if (it != g_modules.end() && mods) {
+            (*mods)[c] = it->second;
             continue;
         }
         std::ifstream f(dir + "/" + key[c] + ".cubin", std::ios::binary);
         if (f) cubin[c].assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
         if (cubin[c].empty()) todo.push_back(c);
     }
+    if (compiled) *compiled = (int)todo.size();
     if (!todo.empty()) {
         unsigned hw = std::thread::hardware_concurrency();
         const int nthreads = (int)std::max(1u, std::min<unsigned>(hw ? hw : 4, (unsigned)todo.size()));
@@ -663,6 +683,33 @@ std::string jit_build(const Schedule &S, int n, bool dbl_state, JitProgram &out)
             }
         }
     }
+    return "";
+}
+
+}  // namespace
+
+std::string jit_precompile(const Schedule &S, int n, bool dbl_state, int *compiled) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    init_locked();
+    if (!g_nvrtc.ok) return g_why.empty() ? "NVRTC unavailable" : g_why;
+    std::vector<std::string> key, cubin;
+    return chunk_cubins(S, n, dbl_state, key, cubin, nullptr, compiled);
+}
+
+// Passes are compiled in chunks (one NVRTC program each, on a pool of host
+// threads); each chunk's cubin is cached in memory and on disk by the hash of
+// its source.
+std::string jit_build(const Schedule &S, int n, bool dbl_state, JitProgram &out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    init_locked();
+    if (!(g_nvrtc.ok && g_drv.ok)) return g_why;
+    const int P = (int)S.passes.size();
+    const int chunk = kChunk;
+    const int nchunks = (P + chunk - 1) / chunk;
+    std::vector<std::string> key, cubin;
+    std::vector<CUmodule> mods;
+    std::string e = chunk_cubins(S, n, dbl_state, key, cubin, &mods, nullptr);
+    if (!e.empty()) return e;
     for (int c = 0; c < nchunks; c++) {
         if (mods[c]) continue;
         if (g_drv.load(&mods[c], cubin[c].data()) != CUDA_SUCCESS) return "cuModuleLoadData failed";

@@ -27,6 +27,10 @@ bool jit_available(std::string *why);
 // interpreter kernel).
 std::string jit_build(const Schedule &S, int n, bool dbl, JitProgram &out);
 
+// Compile S's kernels into the disk cache without loading them (no GPU
+// needed); *compiled (may be NULL) receives the number of chunks compiled.
+std::string jit_precompile(const Schedule &S, int n, bool dbl, int *compiled);
+
 // The generated source of S's kernels, and a compile-only check of it
 // (returns "" or the compiler's log); both need no GPU.
 std::string jit_source(const Schedule &S, int n, bool dbl);

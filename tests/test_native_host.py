@@ -174,3 +174,26 @@ def test_grouping_variants_match_oracle(sd):
             assert got == ref, (h.n, h.m, g)
     with pytest.raises(sd.SDError):
         sd.Simulator(cases[0].n, cases[0].x, cases[0].z, cases[0].c).plan(grouping=4)
+
+
+def test_precompile_generated_kernels(sd, tmp_path, monkeypatch):
+    """The pass kernels generated at run time compile with NVRTC for sm_103a
+    on the host alone (no GPU): the Heisenberg step (complex64), a random
+    k-local Hamiltonian with CNOT permutations and S/CZ layers (complex128,
+    fixed point), and a large diagonal group; a second call finds them all
+    in the on-disk cache."""
+    monkeypatch.setenv("SD_JIT_CACHE", str(tmp_path))
+    h = heisenberg_lattice(4, 5)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    assert sim.precompile(sd.C64, 1, 1) >= 1
+    assert sim.precompile(sd.C64, 1, 1) == 0
+    rng = np.random.default_rng(95)
+    hr = random_klocal(20, 40, rng, weights=(2, 3))
+    simr = sd.Simulator(hr.n, hr.x, hr.z, hr.c).plan(skip_rule=0)
+    assert simr.precompile(sd.C128, 1, 1) >= 1
+    z = rng.integers(1, 1 << 20, size=1500, dtype=np.uint64)
+    hz = sd.Simulator(20, np.zeros(1500, dtype=np.uint64), z, rng.uniform(-1, 1, 1500)).plan()
+    assert hz.precompile(sd.C64, 1, 1) >= 1
+    assert len(list(tmp_path.glob("*.cubin"))) >= 3
+    small = tfim_chain(10)
+    assert sd.Simulator(small.n, small.x, small.z, small.c).plan().precompile(sd.C64, 5, 1) == 0
