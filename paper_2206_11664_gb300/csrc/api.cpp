@@ -1234,6 +1234,8 @@ struct BatchEntry {
     std::vector<BatchGroup> groups;
 };
 std::recursive_mutex g_batch_mu;
+// An instance with 2^8 or more tiles (a tile per SM at least) runs on its own.
+constexpr int kBatchAloneTileBits = 8;
 std::list<BatchEntry> g_batches;   // most recent first
 constexpr size_t kBatchCache = 8;
 
@@ -1314,7 +1316,10 @@ sd_status batch_entry(sd_ctx *const *ctxs, void *const *d_states, int64_t count,
             else if (K < 0) K = p->sched.K;
             else if (K != p->sched.K) mixed = true;
         }
-        if (mixed || K < 0) {
+        // Instances large enough to fill the GPU on their own run like
+        // sd_evolve, with their passes compiled at run time; the rest share
+        // the level launches of the interpreter kernel.
+        if (mixed || K < 0 || (it.ctx->n - K >= kBatchAloneTileBits && jit_wanted(it.ctx, true, it.prog[1]->passes))) {
             // run like sd_evolve; build its block programs now
             sd_status s = evolve_impl(it.ctx, it.psi, dbl, dt, steps, order, st, false);
             if (s != SD_OK) return s;

@@ -306,6 +306,27 @@ def test_batch_matches_individual(sd):
         assert np.linalg.norm(_host(t) - r) < 1e-4
 
 
+def test_batch_with_large_instance(sd):
+    """A batch mixing an instance large enough to run on its own (n = 21,
+    passes compiled at run time) with small ones sharing the level launches
+    gives what separate sd_evolve calls give."""
+    import torch
+    rng = np.random.default_rng(93)
+    sims, states, refs = [], [], []
+    for n in (15, 21, 16):
+        h = random_klocal(n, 50, rng, weights=(2, 3))
+        psi = _rand_state(rng, n)
+        sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+        sims.append(sim)
+        states.append(_dev(psi, "c64"))
+        r = _dev(psi, "c64")
+        sim.evolve(r, 0.01, 3, 2)
+        refs.append(r)
+    sd.evolve_batch(sims, states, 0.01, 3, 2)
+    for t, r in zip(states, refs):
+        assert torch.linalg.vector_norm((t - r).to(torch.complex128)).item() < 1e-5
+
+
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 def test_autotune_tile_size(sd, dtype):
     """The autotuner times tile sizes on its own scratch state, keeps the
