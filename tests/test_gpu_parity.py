@@ -259,6 +259,23 @@ def test_gradient_vs_oracle(sd, order, n):
     assert np.allclose(_host(t), psi0)   # state0 untouched
 
 
+@pytest.mark.parametrize("jit", [-1, 1])
+def test_gradient_complex64(sd, jit):
+    """Complex64 states with FP64 reductions in the adjoint: value and
+    gradient against the complex128 oracle (tile path, both orders)."""
+    rng = np.random.default_rng(57 + jit)
+    n = 14
+    h = gradient_2local(n=n, m=24, rng=rng)
+    psi0 = plus_state(n)
+    obs = z_average_observable(n)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(jit=jit)
+    for order in (1, 2):
+        f, g = sim.grad(_dev(psi0, "c64"), 0.05, 4, obs, order)
+        f_ref, g_ref = oracle.grad(h, psi0, 0.05, 4, order, obs)
+        assert abs(f - f_ref) < 1e-5
+        assert np.max(np.abs(g - g_ref)) < 1e-4 * max(1.0, np.max(np.abs(g_ref)))
+
+
 def test_gradient_autograd_function(sd):
     import torch
     rng = np.random.default_rng(77)
