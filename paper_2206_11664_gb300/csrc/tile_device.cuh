@@ -131,26 +131,12 @@ __device__ __forceinline__ void wht16(double *G) {
             }
 }
 
-// e^{-2 pi i t} of Q0.64 turns t (times sc) applied to a: the top 8 bits of t
+// e^{-2 pi i t} (times sc) applied to a, for turns t: the top 8 bits of t
 // index a table of e^{2 pi i k/256}; the remaining angle phi < 2 pi/256 goes
 // through the Taylor series of cos and sin (truncation error below 1e-10 in
-// single precision and 1e-18 in double precision).
-__device__ __forceinline__ float2 rotate_tw(float2 a, uint64_t t, const float2 *__restrict__ tw, float sc) {
-    const float2 e = tw[t >> 56];
-    const uint32_t r = (uint32_t)((t << 8) >> 32);
-    const float phi = (float)r * (float)(6.283185307179586 / 256.0 / 4294967296.0);
-    const float p2 = phi * phi;
-    const float cp = fmaf(p2, fmaf(p2, 1.0f / 24.0f, -0.5f), 1.0f);
-    const float sp = phi * fmaf(p2, -1.0f / 6.0f, 1.0f);
-    const float C = (e.x * cp - e.y * sp) * sc;
-    const float S = (e.y * cp + e.x * sp) * sc;
-    float2 o;
-    o.x = a.x * C + a.y * S;
-    o.y = a.y * C - a.x * S;
-    return o;
-}
-// The same rotation for Q0.32 turns (single precision): the top 8 bits index
-// the table, the low 24 bits are the remaining angle, exact in a float.
+// single precision and 1e-18 in double precision).  Single precision takes
+// Q0.32 turns (the low 24 bits, exact in a float, are the remaining angle);
+// double precision takes Q0.64 turns.
 __device__ __forceinline__ float2 rotate_tw32(float2 a, uint32_t t, const float2 *__restrict__ tw, float sc) {
     const float2 e = tw[t >> 24];
     const float phi = (float)(t & 0xffffffu) * (float)(6.283185307179586 / 4294967296.0);
