@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsd.so")
 SOURCES = ["planner.cpp", "schedule.cpp", "api.cpp", "jit.cpp", "kernels.cu", "noalloc.cu"]
-JIT_HEADERS = [("kJitDevTypes", "dev_types.h"), ("kJitTileDevice", "tile_device.cuh")]
+JIT_HEADERS = [("kJitDevTypes", "dev_types.h"), ("kJitFixedPoint", "fixed_point.cuh"),
+               ("kJitTileDevice", "tile_device.cuh")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

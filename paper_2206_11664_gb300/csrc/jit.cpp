@@ -31,7 +31,7 @@
 #include <vector>
 
 #include "jit.h"
-#include "jit_headers.inc"   // kJitDevTypes, kJitTileDevice: the two device headers as text
+#include "jit_headers.inc"   // kJitDevTypes, kJitFixedPoint, kJitTileDevice: the device headers as text
 
 namespace sd {
 namespace {
@@ -571,9 +571,9 @@ void mkdirs(const std::string &p) {
 
 std::string compile_cubin(const std::string &src, std::string &cubin) {
     nvrtcProgram prog;
-    const char *hdrs[] = {kJitDevTypes, kJitTileDevice};
-    const char *names[] = {"dev_types.h", "tile_device.cuh"};
-    if (g_nvrtc.create(&prog, src.c_str(), "sd_passes.cu", 2, hdrs, names) != NVRTC_SUCCESS)
+    const char *hdrs[] = {kJitDevTypes, kJitFixedPoint, kJitTileDevice};
+    const char *names[] = {"dev_types.h", "fixed_point.cuh", "tile_device.cuh"};
+    if (g_nvrtc.create(&prog, src.c_str(), "sd_passes.cu", 3, hdrs, names) != NVRTC_SUCCESS)
         return "nvrtcCreateProgram failed";
     const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG"};
     nvrtcResult rc = g_nvrtc.compile(prog, 4, opts);
@@ -627,6 +627,13 @@ namespace {
 
 constexpr int kChunk = 12;   // passes per NVRTC program
 
+// Hash of the device headers the generated sources include: part of the
+// cache key, so that cached kernels of an older library are not reused.
+size_t headers_hash() {
+    static const size_t h = std::hash<std::string>{}(std::string(kJitDevTypes) + kJitFixedPoint + kJitTileDevice);
+    return h;
+}
+
 // Sources, cache keys and cubins of S's pass chunks: cubins come from the
 // in-memory module table (left empty, mods[c] set), the disk cache, or NVRTC
 // (compiled on a pool of host threads and written to the disk cache).
@@ -646,7 +653,7 @@ std::string chunk_cubins(const Schedule &S, int n, bool dbl_state, std::vector<s
     for (int c = 0; c < nchunks; c++) {
         code[c] = source_range(S, n, dbl_state, c * kChunk, std::min(P, (c + 1) * kChunk));
         key[c] = std::to_string(std::hash<std::string>{}(code[c])) + "_" + std::to_string(code[c].size()) +
-                 "_nvrtc" + std::to_string(maj) + "." + std::to_string(min);
+                 "_h" + std::to_string(headers_hash()) + "_nvrtc" + std::to_string(maj) + "." + std::to_string(min);
         auto it = g_modules.find(key[c]);
         if (it != g_modules.end() && mods) {
             (*mods)[c] = it->second;
