@@ -197,3 +197,36 @@ def test_precompile_generated_kernels(sd, tmp_path, monkeypatch):
     assert len(list(tmp_path.glob("*.cubin"))) >= 3
     small = tfim_chain(10)
     assert sd.Simulator(small.n, small.x, small.z, small.c).plan().precompile(sd.C64, 5, 1) == 0
+
+
+def test_argument_validation_of_the_other_entry_points(sd):
+    """Argument errors of the entry points added beside sd_evolve are
+    reported before any device work (no GPU needed)."""
+    from paper_2206_11664_gb300 import _native as N
+    lib = N.load()
+    h = heisenberg_lattice(3, 3)
+    unplanned = sd.Simulator(h.n, h.x, h.z, h.c)
+    best = ctypes.c_int(0)
+    cnt = ctypes.c_int64(0)
+    assert lib.sd_autotune(unplanned._h, N.SD_C64, 0.1, 4, 1, 11, 13, ctypes.byref(best), None) == N.SD_ENOPLAN
+    assert lib.sd_precompile(unplanned._h, N.SD_C64, 1, 1, ctypes.byref(cnt)) == N.SD_ENOPLAN
+    assert lib.sd_count_passes(unplanned._h, N.SD_C64, 1, 1, ctypes.byref(cnt)) == N.SD_ENOPLAN
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    for kmin, kmax in ((8, 13), (12, 14), (13, 12)):
+        assert lib.sd_autotune(sim._h, N.SD_C64, 0.1, 4, 1, kmin, kmax, ctypes.byref(best), None) == N.SD_EINVAL
+    assert lib.sd_autotune(sim._h, N.SD_C64, 0.1, 0, 1, 11, 13, ctypes.byref(best), None) == N.SD_EINVAL
+    assert lib.sd_autotune(sim._h, N.SD_C64, float("nan"), 4, 1, 11, 13, ctypes.byref(best), None) == N.SD_EINVAL
+    assert lib.sd_autotune(sim._h, 7, 0.1, 4, 1, 11, 13, ctypes.byref(best), None) == N.SD_EINVAL
+    assert lib.sd_precompile(sim._h, N.SD_C64, 1, 3, ctypes.byref(cnt)) == N.SD_EINVAL
+    assert lib.sd_precompile(sim._h, 7, 1, 1, ctypes.byref(cnt)) == N.SD_EINVAL
+    assert lib.sd_precompile(sim._h, N.SD_C64, -1, 1, ctypes.byref(cnt)) == N.SD_EINVAL
+    assert lib.sd_count_passes(sim._h, N.SD_C64, 1, -1, ctypes.byref(cnt)) == N.SD_EINVAL
+    assert lib.sd_prepare(None, N.SD_C64, 0.1, 1, 1) == N.SD_EINVAL
+    assert lib.sd_prepare(sim._h, N.SD_C64, 0.1, 1, 5) == N.SD_EINVAL
+    assert lib.sd_prepare(sim._h, N.SD_C64, float("inf"), 1, 1) == N.SD_EINVAL
+    assert lib.sd_prepare_batch(None, None, 1, N.SD_C64, 0.1, 1, 1) == N.SD_EINVAL
+    hs = (ctypes.c_void_p * 1)(sim._h)
+    ps = (ctypes.c_void_p * 1)(None)
+    assert lib.sd_prepare_batch(hs, ps, -1, N.SD_C64, 0.1, 1, 1) == N.SD_EINVAL
+    assert lib.sd_prepare_batch(hs, ps, 70000, N.SD_C64, 0.1, 1, 1) == N.SD_EINVAL
+    assert lib.sd_evolve_host(sim._h, None, None, N.SD_C64, 0.1, 1, 1, None) == N.SD_EINVAL
