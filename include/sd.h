@@ -133,13 +133,16 @@ sd_status sd_create_str(int n, int64_t m, const char *const *paulis, const doubl
  * device programs built for the old coefficients are dropped. */
 sd_status sd_set_coeffs(sd_ctx *ctx, const double *coeffs);
 
-/* Host planning: greedy first-fit partition into commuting groups (Sec. 2.3),
+/* Host planning: greedy partition into commuting groups (Sec. 2.3; first
+ * fit in input order unless opts->grouping chooses another order),
  * independent generators (Appendix, Algorithm 6) completed to n commuting
  * rows, synthesis steps (i)-(iv) (Algorithms 2-5), and masks/signs of every
  * term by replaying the circuit on the full tableau (Eq. hami_sim_diag).
  * opts may be NULL.  Host only: no device memory is touched here. */
 sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts);
 
+/* Fills *out with a read-only view of the plan (layout in sd_plan_view);
+ * SD_ENOPLAN before sd_plan.  Host only. */
 sd_status sd_get_plan(const sd_ctx *ctx, sd_plan_view *out);
 
 /* Statistics of the pass schedule that sd_evolve would run for this dtype
