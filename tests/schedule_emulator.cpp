@@ -1,0 +1,214 @@
+// Host emulation of a tile-pass schedule, for the CPU tests.
+//
+// It plans and schedules a Trotter step with the library's own host code
+// (planner.cpp, schedule.cpp). Then it executes the schedule on a complex128
+// state with plain loops, following what the device passes do:
+//   - tiles of 2^K amplitudes;
+//   - rounds of one-qubit Cliffords on register positions;
+//   - quarter-turn layers;
+//   - group exponentials assembled from the staged term slots, tile constants
+//     and class structure;
+//   - tile permutations on the exchange;
+//   - the deferred Hadamard scale.
+// The result is written out, and tests/test_schedule_emulation.py compares it
+// with the oracle.
+//
+// This checks the scheduler's encoding of the step: op placement, slot and
+// class bookkeeping, permutation columns and scale folding. It needs no GPU.
+// The device kernels implement the same semantics, and the GPU parity tests
+// check them.
+//
+// Usage: schedule_emulator <input> <output>.
+// The input is binary, in this order: int32 n, int64 m, int32 skip_rule,
+// int32 K, int32 c, int32 order, int64 steps, float64 dt, uint64 x[m],
+// uint64 z[m], float64 coeffs[m], complex128 psi[2^n]. The output is
+// complex128 psi[2^n].
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sd_internal.h"
+
+namespace sd {
+void set_last_error(const std::string &) {}
+}  // namespace sd
+
+using namespace sd;
+using cd = std::complex<double>;
+
+namespace {
+
+int popc(uint64_t v) { return __builtin_popcountll(v); }
+
+cd ipow(cd v, int k) {
+    switch (k & 3) {
+    case 1: return cd(-v.imag(), v.real());
+    case 2: return -v;
+    case 3: return cd(v.imag(), -v.real());
+    default: return v;
+    }
+}
+
+struct Emulator {
+    int n;
+    const Schedule &S;
+    std::vector<cd> &psi;
+
+    void run_pass(const DevPass &P) {
+        const int K = S.K;
+        const int T = 1 << K;
+        std::vector<cd> a(T), b(T);
+        std::vector<uint64_t> spread(T);
+        for (int l = 0; l < T; l++) {
+            uint64_t x = 0;
+            for (int p = 0; p < K; p++)
+                if ((l >> p) & 1) x |= uint64_t(1) << P.tile_bits[p];
+            spread[l] = x;
+        }
+        const double pass_scale = P.scale_in_diag ? 1.0 : P.scale;
+        for (uint64_t o = 0; o < (uint64_t(1) << P.n_outer); o++) {
+            uint64_t xo = 0;
+            for (int k = 0; k < P.n_outer; k++)
+                if ((o >> k) & 1) xo |= uint64_t(1) << P.outer_bits[k];
+            for (int l = 0; l < T; l++) a[l] = psi[xo | spread[l]];
+            for (int r = P.round_begin; r < P.round_begin + P.n_rounds; r++) {
+                const DevRound &R = S.rounds[r];
+                for (int oi = R.op_begin; oi < R.op_end; oi++) op(S.ops[oi], R, P, xo, o, spread, a);
+                if (R.perm >= 0) {
+                    const DevPerm &pm = S.perms[R.perm];
+                    for (int l = 0; l < T; l++) {
+                        uint32_t t = 0;
+                        for (int p = 0; p < K; p++)
+                            if ((l >> p) & 1) t ^= pm.col[p];
+                        for (int k = 0; k < P.n_outer; k++)
+                            if ((o >> k) & 1) t ^= pm.ocol[k];
+                        b[t] = a[l];
+                    }
+                    a.swap(b);
+                }
+            }
+            for (int l = 0; l < T; l++) psi[xo | spread[l]] = a[l] * pass_scale;
+        }
+    }
+
+    void op(const DevOp &op, const DevRound &R, const DevPass &P, uint64_t xo, uint64_t o,
+            const std::vector<uint64_t> &spread, std::vector<cd> &a) {
+        const int T = (int)a.size();
+        if (op.kind == D_HAD || op.kind == D_MONO) {
+            const int bit = 1 << R.reg_pos[op.slot];
+            for (int l = 0; l < T; l++) {
+                if (l & bit) continue;
+                const cd u = a[l], w = ipow(a[l | bit], c1_a(op.arg));
+                if (op.kind == D_HAD) {
+                    a[l] = u + w;
+                    a[l | bit] = ipow(u - w, c1_b(op.arg));
+                } else if (c1_x(op.arg)) {
+                    a[l] = w;
+                    a[l | bit] = u;
+                } else {
+                    a[l | bit] = w;
+                }
+            }
+        } else if (op.kind == D_PHASE) {
+            const DevPhase &ph = S.phases[op.arg];
+            for (int l = 0; l < T; l++) {
+                const uint64_t x = xo | spread[l];
+                int k = popc(x & ph.sp) - popc(x & ph.sm);
+                int q = 0;
+                for (int c = 0; c < n; c++)
+                    if ((x >> c) & 1) q ^= popc(x & S.mask_pool[ph.up_base + c]) & 1;
+                a[l] = ipow(a[l], k + 2 * q);
+            }
+        } else if (op.kind == D_DIAG) {
+            const DevDiag &d = S.diags[op.arg];
+            auto slot_sum = [&](int j) {   // signed angle sum of slot j over the tile's outer bits
+                const DevSlot &sl = S.slots[R.slot_begin + j];
+                uint64_t acc = 0;
+                for (int t = sl.tb; t < sl.tb + sl.tn; t++) {
+                    const uint64_t q = (uint64_t)S.term_q[t];
+                    acc += (popc(xo & S.term_mo[t]) & 1) ? (0 - q) : q;
+                }
+                return acc;
+            };
+            uint64_t cst = 0;
+            if (d.cst >= 0)
+                for (int t = R.cst_begin[d.cst]; t < R.cst_begin[d.cst] + R.cst_count[d.cst]; t++) {
+                    const uint64_t q = (uint64_t)S.cst_q[t];
+                    cst += (popc(xo & S.cst_mo[t]) & 1) ? (0 - q) : q;
+                }
+            const double sc = op.pad ? P.scale : 1.0;
+            for (int l = 0; l < T; l++) {
+                int s = 0;
+                for (int i = 0; i < 4; i++) s |= ((l >> R.reg_pos[i]) & 1) << i;
+                uint64_t angle = 0;
+                for (int u = 0; u < 16; u++) {
+                    uint64_t G = (u == 0) ? cst : 0;
+                    if (d.zs[u] >= 0) G += slot_sum(d.zs[u]);
+                    for (int j = d.off[u]; j < d.off[u + 1]; j++) {
+                        const uint64_t Q = slot_sum(j);
+                        G += (popc((uint64_t)l & S.slots[R.slot_begin + j].ml) & 1) ? (0 - Q) : Q;
+                    }
+                    angle += (popc((uint64_t)(s & u)) & 1) ? (0 - G) : G;
+                }
+                const double turns = (double)(int64_t)angle / 18446744073709551616.0;
+                a[l] *= std::polar(sc, -2.0 * M_PI * turns);
+            }
+        }
+    }
+};
+
+}  // namespace
+
+int main(int argc, char **argv) {
+    if (argc != 3) return 2;
+    FILE *f = std::fopen(argv[1], "rb");
+    if (!f) return 2;
+    int32_t n, skip, K, c, order;
+    int64_t m, steps;
+    double dt;
+    bool ok = std::fread(&n, 4, 1, f) == 1 && std::fread(&m, 8, 1, f) == 1 && std::fread(&skip, 4, 1, f) == 1 &&
+              std::fread(&K, 4, 1, f) == 1 && std::fread(&c, 4, 1, f) == 1 && std::fread(&order, 4, 1, f) == 1 &&
+              std::fread(&steps, 8, 1, f) == 1 && std::fread(&dt, 8, 1, f) == 1;
+    std::vector<uint64_t> x(m), z(m);
+    std::vector<double> coef(m);
+    std::vector<cd> psi((size_t)1 << n);
+    ok = ok && std::fread(x.data(), 8, m, f) == (size_t)m && std::fread(z.data(), 8, m, f) == (size_t)m &&
+         std::fread(coef.data(), 8, m, f) == (size_t)m && std::fread(psi.data(), 16, psi.size(), f) == psi.size();
+    std::fclose(f);
+    if (!ok) return 2;
+    Plan plan;
+    std::string e = make_plan(n, m, x.data(), z.data(), skip, plan);
+    if (!e.empty()) {
+        std::fprintf(stderr, "plan: %s\n", e.c_str());
+        return 1;
+    }
+    // one step: groups 1..G (first order) or the Strang sequence (second order)
+    const int G = (int)plan.groups.size();
+    Circuit circ;
+    if (order == 1 || G == 1) {
+        for (int g = 0; g < G; g++) append_group_step(plan, g, 1.0, dt, coef, circ);
+    } else {
+        for (int g = 0; g < G - 1; g++) append_group_step(plan, g, 0.5, dt, coef, circ);
+        append_group_step(plan, G - 1, 1.0, dt, coef, circ);
+        for (int g = G - 2; g >= 0; g--) append_group_step(plan, g, 0.5, dt, coef, circ);
+    }
+    canonicalize_1q(circ, n);
+    Schedule S;
+    e = schedule_circuit(circ, n, K, c, S);
+    if (!e.empty()) {
+        std::fprintf(stderr, "schedule: %s\n", e.c_str());
+        return 1;
+    }
+    Emulator em{n, S, psi};
+    for (int64_t s = 0; s < steps; s++)
+        for (const DevPass &P : S.passes) em.run_pass(P);
+    f = std::fopen(argv[2], "wb");
+    if (!f) return 2;
+    std::fwrite(psi.data(), 16, psi.size(), f);
+    std::fclose(f);
+    std::printf("passes %zu rounds %zu\n", S.passes.size(), S.rounds.size());
+    return 0;
+}

@@ -1,0 +1,76 @@
+"""The pass schedule of a Trotter step, executed on the CPU.
+
+tests/schedule_emulator.cpp plans and schedules with the library's host
+code, then executes the tile passes with plain loops. The result must match
+the oracle. This covers op placement, term slots and class structure, tile
+constants, CNOT permutation columns, quarter-turn layers and the deferred
+Hadamard scale, for several tile sizes, skip rules and both orders, without
+a GPU."""
+import os
+import shutil
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import planner as P
+from workloads import heisenberg_lattice, jw_like, neel_index, random_klocal, tfim_chain
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "..", "paper_2206_11664_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def emulator(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path_factory.mktemp("emu") / "schedule_emulator")
+    subprocess.check_call([cxx, "-O2", "-std=c++17", "-I", CSRC, "-I", "/usr/local/cuda/include",
+                           os.path.join(HERE, "schedule_emulator.cpp"), os.path.join(CSRC, "planner.cpp"),
+                           os.path.join(CSRC, "schedule.cpp"), "-o", exe])
+    return exe
+
+
+def _run(exe, tmp_path, h, psi0, dt, steps, order, skip, K, c):
+    inp, out = tmp_path / "in.bin", tmp_path / "out.bin"
+    with open(inp, "wb") as f:
+        f.write(struct.pack("<iqiiiiqd", h.n, h.m, skip, K, c, order, steps, dt))
+        f.write(np.ascontiguousarray(h.x, dtype=np.uint64).tobytes())
+        f.write(np.ascontiguousarray(h.z, dtype=np.uint64).tobytes())
+        f.write(np.ascontiguousarray(h.c, dtype=np.float64).tobytes())
+        f.write(np.ascontiguousarray(psi0, dtype=np.complex128).tobytes())
+    r = subprocess.run([exe, str(inp), str(out)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return np.fromfile(out, dtype=np.complex128)
+
+
+def _rand(rng, n):
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return v / np.linalg.norm(v)
+
+
+CASES = [
+    ("random k-local, CNOT and S/CZ layers", lambda rng: random_klocal(11, 40, rng, weights=(2, 3, 4))),
+    ("Heisenberg 3x4", lambda rng: heisenberg_lattice(3, 4)),
+    ("JW-style", lambda rng: jw_like(n=11, m=200, rng=rng)),
+    ("TFIM chain", lambda rng: tfim_chain(12)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("skip", [0, 1, 2])
+def test_schedule_matches_oracle(emulator, tmp_path, case, skip):
+    rng = np.random.default_rng(700 + 10 * case + skip)
+    h = CASES[case][1](rng)
+    groups = P.greedy_partition(h.x, h.z)
+    for order, K, c in ((1, 9, 4), (2, 10, 3), (1, 11, 4)):
+        if K > h.n:
+            continue
+        psi0 = _rand(rng, h.n)
+        got = _run(emulator, tmp_path, h, psi0, 0.05, 2, order, skip, K, c)
+        ref = oracle.evolve(h, psi0, 0.05, 2, order, groups)
+        err = np.linalg.norm(got - ref)
+        assert err < 1e-10, (CASES[case][0], skip, order, K, err)
