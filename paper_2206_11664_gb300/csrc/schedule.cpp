@@ -343,24 +343,50 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
     S.c = c;
     if (K < kRegBits + kLaneBits || K > 13 || n < K) return "invalid tile size";
     const int N = (int)circ.ops.size();
+    // Dependencies, per wire.  Diagonal ops commute with each other; CNOTs
+    // that share a wire in the same role (all controls, or all targets)
+    // commute too, so such a run of CNOTs may execute in any order, each after
+    // what preceded the run.  Everything else keeps program order on a wire.
     std::vector<std::vector<int>> preds(N);
     {
-        std::vector<int> last_nd(n, -1);
-        std::vector<std::vector<int>> diag_since(n);
+        struct Wire {
+            std::vector<int> run;      // current run: CNOTs of one role, or one other op
+            int role = 0;              // 1: run of controls, 2: run of targets, 0: other
+            std::vector<int> before;   // what the run follows
+            std::vector<int> diags;    // diagonal ops since the run began
+        };
+        std::vector<Wire> W(n);
         for (int j = 0; j < N; j++) {
             const FlatOp &op = circ.ops[j];
-            bool isdiag = op.kind == OK_PHASE || op.kind == OK_DIAG;
+            const bool isdiag = op.kind == OK_PHASE || op.kind == OK_DIAG;
             std::set<int> p;
-            for (int w : wires_of(op, n)) {
-                if (last_nd[w] >= 0) p.insert(last_nd[w]);
-                if (!isdiag)
-                    for (int d : diag_since[w]) p.insert(d);
+            if (isdiag) {
+                for (int w : wires_of(op, n)) p.insert(W[w].run.begin(), W[w].run.end());
+                for (int w : wires_of(op, n)) W[w].diags.push_back(j);
+            } else {
+                std::vector<std::pair<int, int>> roles;   // (wire, role)
+                if (op.kind == OK_CNOT) roles = {{op.q, 1}, {op.q2, 2}};
+                else roles = {{op.q, 0}};
+                for (auto &wr : roles) {
+                    const Wire &s = W[wr.first];
+                    if (wr.second != 0 && s.role == wr.second) p.insert(s.before.begin(), s.before.end());
+                    else p.insert(s.run.begin(), s.run.end());
+                    p.insert(s.diags.begin(), s.diags.end());
+                }
+                for (auto &wr : roles) {
+                    Wire &s = W[wr.first];
+                    if (wr.second != 0 && s.role == wr.second) {
+                        s.run.push_back(j);
+                    } else {
+                        s.before = s.run;
+                        s.before.insert(s.before.end(), s.diags.begin(), s.diags.end());
+                        s.run.assign(1, j);
+                        s.role = wr.second;
+                        s.diags.clear();
+                    }
+                }
             }
             preds[j].assign(p.begin(), p.end());
-            for (int w : wires_of(op, n)) {
-                if (isdiag) diag_since[w].push_back(j);
-                else { last_nd[w] = j; diag_since[w].clear(); }
-            }
         }
     }
     std::vector<int> done(N, -1);   // global round id in which the op ran
