@@ -15,7 +15,7 @@ from oracle import planner as P
 from workloads import (from_strings, heisenberg_lattice, jw_like, neel_index, random_klocal,
                        tfim_chain, basis_state, plus_state, product_state, haar_product_factors,
                        tfim_fully_connected, syk_majorana,
-                       gradient_2local, z_average_observable, batch_instances)
+                       gradient_2local, z_average_observable)
 
 pytestmark = pytest.mark.gpu
 

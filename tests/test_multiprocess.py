@@ -43,3 +43,17 @@ def test_two_ranks_gloo():
         assert w == 2 and local == r
         assert t_max == pytest.approx(1.5)
         assert value == pytest.approx(2 * 20 / 1.5)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under a multi-rank launch the oracle arm runs on rank 0 only: another
+    rank exits 0 at once and prints nothing."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                       env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""

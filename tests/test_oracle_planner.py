@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import planner as P
-from workloads import (from_strings, heisenberg_lattice, pauli_to_masks, tfim_chain,
+from workloads import (heisenberg_lattice, pauli_to_masks, tfim_chain,
                        random_klocal, jw_like, gradient_2local)
 from tests import dense as D
 

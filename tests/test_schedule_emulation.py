@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 from oracle import planner as P
-from workloads import heisenberg_lattice, jw_like, neel_index, random_klocal, tfim_chain
+from workloads import heisenberg_lattice, jw_like, random_klocal, tfim_chain
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "..", "paper_2206_11664_gb300", "csrc")
