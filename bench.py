@@ -172,13 +172,21 @@ DT = 0.02
 TRAFFIC_PER_LAUNCH = {28: 4.235e9, 30: 16.94e9}
 
 
-def cpu_oracle_sample(h, neel, budget_s=15.0, psi=None):
+def cpu_oracle_sample(h, neel, budget_s=15.0, psi=None, threads=None):
     """Oracle (one rotation at a time, complex128, OpenMP on the host cores)
     on a bounded sample of one Trotter step: the first k rotations of the
     grouped order, timed and scaled to the step's m rotations.  psi (the
-    2^n host state) is reused when given."""
+    2^n host state) is reused when given; threads (default: all cores)
+    sets the OpenMP thread count for this sample only."""
     import oracle
     from oracle import planner as P
+    if threads is not None:
+        all_threads = oracle.num_threads()
+        oracle.set_threads(threads)
+        try:
+            return cpu_oracle_sample(h, neel, budget_s, psi)
+        finally:
+            oracle.set_threads(all_threads)
     groups = P.greedy_partition(h.x, h.z)
     seq = [j for g in groups for j in g]
     if psi is None:
@@ -380,7 +388,15 @@ def main():
         del host, dst
         torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_oracle_sample(h, neel)
+        # all host cores, then one core, on the same host state
+        psi = np.zeros(N, dtype=np.complex128)
+        psi[neel] = 1.0
+        cb = cpu_oracle_sample(h, neel, budget_s=12.0, psi=psi)
+        one = cpu_oracle_sample(h, neel, budget_s=8.0, psi=psi, threads=1)
+        cb["one_core"] = {"value": one["value"], "unit": one["unit"], "cores": one["cores"],
+                          "sample": one["sample"]}
+        out["cpu_baseline"] = cb
+        del psi
     if rank == 0:
         print(json.dumps(out))
 
