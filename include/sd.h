@@ -209,7 +209,10 @@ sd_status sd_evolve(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt, int64
 
 /* As sd_evolve, and after every step writes <psi|O|psi> for the Pauli-sum
  * observable O = sum_k oc[k] P_(ox[k], oz[k]) into d_trace[step] (device
- * memory, `steps` doubles, caller-owned). */
+ * memory, `steps` doubles, caller-owned).  The host arrays ox, oz, oc are
+ * copied in stream order before the call returns and may be reused at once;
+ * a later call on the same stream with another observable does not disturb
+ * this one. */
 sd_status sd_evolve_observe(sd_ctx *ctx, void *d_state, sd_dtype dtype, double dt,
                             int64_t steps, int order, int64_t mo, const uint64_t *ox,
                             const uint64_t *oz, const double *oc, double *d_trace,

@@ -555,8 +555,12 @@ struct StagedObs {
     std::vector<double> oc;
 };
 
+// The copies are ordered on the call's stream, so that a new observable does
+// not overwrite the one that an earlier asynchronous call on the same stream
+// (sd_evolve_observe) has still to read.  Their host sources may be freed on
+// return: copies from pageable memory are staged before the call returns.
 sd_status stage_obs(sd_ctx *ctx, int64_t mo, const uint64_t *ox, const uint64_t *oz, const double *oc,
-                    StagedObs &so) {
+                    StagedObs &so, cudaStream_t st) {
     std::vector<uint64_t> dz;
     std::vector<double> dcv;
     so = StagedObs{};
@@ -584,13 +588,16 @@ sd_status stage_obs(sd_ctx *ctx, int64_t mo, const uint64_t *ox, const uint64_t 
     so.dz = p;
     so.dc = reinterpret_cast<const double *>(p + dz.size());
     if (!dz.empty()) {
-        CK(cudaMemcpy(p, dz.data(), sizeof(uint64_t) * dz.size(), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(p + dz.size(), dcv.data(), sizeof(double) * dcv.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(p, dz.data(), sizeof(uint64_t) * dz.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(p + dz.size(), dcv.data(), sizeof(double) * dcv.size(), cudaMemcpyHostToDevice,
+                           st));
     }
     uint64_t *q = p + 2 * dz.size();
-    CK(cudaMemcpy(q, ox, sizeof(uint64_t) * mo, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(q + mo, oz, sizeof(uint64_t) * mo, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(q + 2 * mo, oc, sizeof(double) * mo, cudaMemcpyHostToDevice));
+    if (mo > 0) {
+        CK(cudaMemcpyAsync(q, ox, sizeof(uint64_t) * mo, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(q + mo, oz, sizeof(uint64_t) * mo, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(q + 2 * mo, oc, sizeof(double) * mo, cudaMemcpyHostToDevice, st));
+    }
     return SD_OK;
 }
 
@@ -1082,7 +1089,7 @@ sd_status sd_evolve_observe(sd_ctx *ctx, void *d_state, sd_dtype dtype, double d
     const bool dbl = dtype == SD_C128;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     StagedObs so;
-    if ((s = stage_obs(ctx, mo, ox, oz, oc, so)) != SD_OK) return s;
+    if ((s = stage_obs(ctx, mo, ox, oz, oc, so, st)) != SD_OK) return s;
     Program *P = nullptr;
     if ((s = get_program(ctx, dbl, order, 0, dt, P)) != SD_OK) return s;
     if (P->onchip && so.ox.empty())
@@ -1120,7 +1127,7 @@ sd_status sd_expect(sd_ctx *ctx, const void *d_state, sd_dtype dtype, int64_t mo
     if ((s = check_obs(ctx, mo, ox, oz, oc)) != SD_OK) return s;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     StagedObs so;
-    if ((s = stage_obs(ctx, mo, ox, oz, oc, so)) != SD_OK) return s;
+    if ((s = stage_obs(ctx, mo, ox, oz, oc, so, st)) != SD_OK) return s;
     if ((s = ensure_partial(ctx, 1)) != SD_OK) return s;
     if ((s = expect_async(ctx, d_state, dtype == SD_C128, so, ctx->d_scalar, st)) != SD_OK) return s;
     double v = 0.0;
@@ -1163,7 +1170,7 @@ sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt, 
     CK(cudaMemcpyAsync(phi, d_state0, bytes, cudaMemcpyDeviceToDevice, st));
     if ((s = evolve_impl(ctx, phi, dbl, dt, steps, order, st)) != SD_OK) return s;
     StagedObs so;
-    if ((s = stage_obs(ctx, mo, ox, oz, oc, so)) != SD_OK) return s;
+    if ((s = stage_obs(ctx, mo, ox, oz, oc, so, st)) != SD_OK) return s;
     if ((s = ensure_partial(ctx, 1)) != SD_OK) return s;
     if ((s = expect_async(ctx, phi, dbl, so, ctx->d_scalar, st)) != SD_OK) return s;
     const uint64_t *ax = staged_all_x(ctx, so);
