@@ -8,6 +8,7 @@ simulator never does, and nothing here imports the simulator.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -36,30 +37,48 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _configure(L):
+    """Argument and result types of the exported routines."""
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_apply_rotation.argtypes = [ctypes.c_int, dp, ctypes.c_uint64,
+                                        ctypes.c_uint64, ctypes.c_double]
+    L.oracle_apply_pauli.argtypes = [ctypes.c_int, dp, dp, ctypes.c_uint64,
+                                     ctypes.c_uint64]
+    L.oracle_apply_sequence.argtypes = [ctypes.c_int, dp, u64p, u64p, ctypes.c_int64,
+                                        i64p, dp, ctypes.c_int64]
+    L.oracle_expect.argtypes = [ctypes.c_int, dp, ctypes.c_int64, u64p, u64p, dp]
+    L.oracle_expect.restype = ctypes.c_double
+    L.oracle_grad.argtypes = [ctypes.c_int, dp, ctypes.c_int64, u64p, u64p, dp,
+                              ctypes.c_int64, i64p, dp, ctypes.c_int64,
+                              ctypes.c_int64, u64p, u64p, dp, dp]
+    L.oracle_grad.restype = ctypes.c_double
+    L.oracle_num_threads.restype = ctypes.c_int
+    L.oracle_set_threads.argtypes = [ctypes.c_int]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            u64p = ctypes.POINTER(ctypes.c_uint64)
-            i64p = ctypes.POINTER(ctypes.c_int64)
-            dp = ctypes.POINTER(ctypes.c_double)
-            L.oracle_apply_rotation.argtypes = [ctypes.c_int, dp, ctypes.c_uint64,
-                                                ctypes.c_uint64, ctypes.c_double]
-            L.oracle_apply_pauli.argtypes = [ctypes.c_int, dp, dp, ctypes.c_uint64,
-                                             ctypes.c_uint64]
-            L.oracle_apply_sequence.argtypes = [ctypes.c_int, dp, u64p, u64p, ctypes.c_int64,
-                                                i64p, dp, ctypes.c_int64]
-            L.oracle_expect.argtypes = [ctypes.c_int, dp, ctypes.c_int64, u64p, u64p, dp]
-            L.oracle_expect.restype = ctypes.c_double
-            L.oracle_grad.argtypes = [ctypes.c_int, dp, ctypes.c_int64, u64p, u64p, dp,
-                                      ctypes.c_int64, i64p, dp, ctypes.c_int64,
-                                      ctypes.c_int64, u64p, u64p, dp, dp]
-            L.oracle_grad.restype = ctypes.c_double
-            L.oracle_num_threads.restype = ctypes.c_int
-            L.oracle_set_threads.argtypes = [ctypes.c_int]
-            _lib = L
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Route every wrapper of this module through another build of the C
+    routines (a copy with a planted mistake, for the tests that check that
+    the pins catch it); the usual library is restored on exit."""
+    global _lib
+    usual = lib()
+    _lib = _configure(ctypes.CDLL(path))
+    try:
+        yield _lib
+    finally:
+        _lib = usual
 
 
 def _p(a, t):
