@@ -153,3 +153,108 @@ def test_planted_sequence_mistake_fails_a_pin(monkeypatch, bad):
             failed.append(name)
             break
     assert failed
+
+
+# ---------------------------------------------------------------- the oracle planner
+
+PLANNER_SRC = os.path.join(os.path.dirname(oracle.__file__), "planner.py")
+
+# (name, text in planner.py, the same text with the mistake planted)
+PLANNER_MUTANTS = [
+    ("H rule without its sign",
+     "        xt, zt = _bit(x, a), _bit(z, a)\n        r ^= xt & zt\n        x = (x",
+     "        xt, zt = _bit(x, a), _bit(z, a)\n        x = (x"),
+    ("S rule moving Z into X",
+     "        z ^= xt << a\n",
+     "        x ^= zt << a\n"),
+    ("CNOT Z rule as printed (z_t ^= z_c)",
+     "        z ^= zt << c\n",
+     "        z ^= zc << t\n"),
+    ("CNOT sign without its last factor",
+     "        r ^= xc & zt & (xt ^ zc ^ 1)\n",
+     "        r ^= xc & zt & (xt ^ zc)\n"),
+    ("CZ rule without its sign",
+     "        r ^= xc & xt & (zt ^ zc)\n",
+     ""),
+    ("vectorised CNOT Z rule as printed",
+     "            Z ^= zt << sc\n",
+     "            Z ^= zc << st\n"),
+    ("Algorithm 2 visiting the qubits first to last",
+     "for i in reversed(range(nA)):",
+     "for i in range(nA):"),
+    ("Algorithm 2 applying H without a strict rank increase",
+     "if r0 < xrank(trial):",
+     "if r0 <= xrank(trial):"),
+    ("Algorithm 6 eliminating above the pivot",
+     "        for k in range(ir + 1, N):\n",
+     "        for k in range(0, ir):\n"),
+    ("Algorithm 4 skipping the S gate",
+     "            if _bit(T[i][1], i):\n                apply(T, (\"S\", i, -1))\n"
+     "                syn.append((\"S\", i, -1))\n",
+     ""),
+    ("skip rule leaving only-X qubits alone",
+     "        if skip_rule >= SKIP_PAPER and has <= {2}:",
+     "        if skip_rule >= SKIP_PAPER and has <= {1, 2}:"),
+    ("first fit ignoring anticommutation",
+     "            if not anti.any():",
+     "            if True:"),
+    ("CNOT map inverse taken in the forward order",
+     "return run(cn), run(list(reversed(cn)))",
+     "return run(cn), run(cn)"),
+]
+
+
+def _planner_pins():
+    from tests import test_oracle_planner as T
+    pins = []
+    for name in sorted(dir(T)):
+        fn = getattr(T, name)
+        if not name.startswith("test_") or not callable(fn):
+            continue
+        marks = [m for m in getattr(fn, "pytestmark", []) if m.name == "parametrize"]
+        if marks:
+            argname, values = marks[0].args[0], marks[0].args[1]
+            pins += [(f"{name}[{v}]", fn, {argname: v}) for v in values]
+        else:
+            pins.append((name, fn, {}))
+    return T, pins
+
+
+def _load_planner(tmp_path, text):
+    import importlib.util
+    path = tmp_path / "planner_copy.py"
+    path.write_text(text)
+    spec = importlib.util.spec_from_file_location("planner_copy", str(path))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _failing_planner_pins(monkeypatch, mod, stop_at_first):
+    T, pins = _planner_pins()
+    monkeypatch.setattr(T, "P", mod)
+    failed = []
+    for name, fn, kw in pins:
+        try:
+            fn(**kw)
+        except (AssertionError, mod.SynthesisError, RuntimeError, ValueError):
+            failed.append(name)
+            if stop_at_first:
+                break
+    return failed
+
+
+def test_unaltered_planner_copy_passes_every_pin(tmp_path, monkeypatch):
+    with open(PLANNER_SRC) as f:
+        mod = _load_planner(tmp_path, f.read())
+    assert len(_planner_pins()[1]) >= 15
+    assert _failing_planner_pins(monkeypatch, mod, stop_at_first=False) == []
+
+
+@pytest.mark.parametrize("name,orig,bad", PLANNER_MUTANTS, ids=[m[0] for m in PLANNER_MUTANTS])
+def test_planted_planner_mistake_fails_a_pin(tmp_path, monkeypatch, name, orig, bad):
+    with open(PLANNER_SRC) as f:
+        text = f.read()
+    assert text.count(orig) == 1, f"the text to alter is not unique in the planner: {orig!r}"
+    mod = _load_planner(tmp_path, text.replace(orig, bad))
+    assert _failing_planner_pins(monkeypatch, mod, stop_at_first=True), f"no pin catches: {name}"
