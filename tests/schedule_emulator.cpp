@@ -18,11 +18,18 @@
 // The device kernels implement the same semantics, and the GPU parity tests
 // check them.
 //
+// A call of several steps is split as the library splits it: first order
+// runs blocks of `reps` steps scheduled as one circuit, then single steps;
+// second order opens with group 1's half step, runs the cores (the
+// step with the half steps of group 1 that meet between consecutive steps
+// merged) in blocks of `reps` and single cores, and closes with the last
+// core, whose group 1 takes a half step.
+//
 // Usage: schedule_emulator <input> <output>.
 // The input is binary, in this order: int32 n, int64 m, int32 skip_rule,
-// int32 K, int32 c, int32 order, int64 steps, float64 dt, uint64 x[m],
-// uint64 z[m], float64 coeffs[m], complex128 psi[2^n]. The output is
-// complex128 psi[2^n].
+// int32 K, int32 c, int32 order, int32 reps, int64 steps, float64 dt,
+// uint64 x[m], uint64 z[m], float64 coeffs[m], complex128 psi[2^n]. The
+// output is complex128 psi[2^n].
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -162,16 +169,25 @@ struct Emulator {
 
 }  // namespace
 
+// Schedules a circuit (one-qubit runs canonicalised first).
+bool schedule(Circuit circ, int n, int K, int c, Schedule &S) {
+    canonicalize_1q(circ, n);
+    const std::string e = schedule_circuit(circ, n, K, c, S);
+    if (!e.empty()) std::fprintf(stderr, "schedule: %s\n", e.c_str());
+    return e.empty();
+}
+
 int main(int argc, char **argv) {
     if (argc != 3) return 2;
     FILE *f = std::fopen(argv[1], "rb");
     if (!f) return 2;
-    int32_t n, skip, K, c, order;
+    int32_t n, skip, K, c, order, reps;
     int64_t m, steps;
     double dt;
     bool ok = std::fread(&n, 4, 1, f) == 1 && std::fread(&m, 8, 1, f) == 1 && std::fread(&skip, 4, 1, f) == 1 &&
               std::fread(&K, 4, 1, f) == 1 && std::fread(&c, 4, 1, f) == 1 && std::fread(&order, 4, 1, f) == 1 &&
-              std::fread(&steps, 8, 1, f) == 1 && std::fread(&dt, 8, 1, f) == 1;
+              std::fread(&reps, 4, 1, f) == 1 && std::fread(&steps, 8, 1, f) == 1 && std::fread(&dt, 8, 1, f) == 1;
+    ok = ok && reps >= 1;
     std::vector<uint64_t> x(m), z(m);
     std::vector<double> coef(m);
     std::vector<cd> psi((size_t)1 << n);
@@ -185,30 +201,72 @@ int main(int argc, char **argv) {
         std::fprintf(stderr, "plan: %s\n", e.c_str());
         return 1;
     }
-    // one step: groups 1..G (first order) or the Strang sequence (second order)
     const int G = (int)plan.groups.size();
-    Circuit circ;
+    auto add = [&](Circuit &circ, int g, double frac) { append_group_step(plan, g, frac, dt, coef, circ); };
+    // one unmerged step: groups 1..G, or the Strang sequence
+    Circuit step;
     if (order == 1 || G == 1) {
-        for (int g = 0; g < G; g++) append_group_step(plan, g, 1.0, dt, coef, circ);
+        for (int g = 0; g < G; g++) add(step, g, 1.0);
     } else {
-        for (int g = 0; g < G - 1; g++) append_group_step(plan, g, 0.5, dt, coef, circ);
-        append_group_step(plan, G - 1, 1.0, dt, coef, circ);
-        for (int g = G - 2; g >= 0; g--) append_group_step(plan, g, 0.5, dt, coef, circ);
+        for (int g = 0; g < G - 1; g++) add(step, g, 0.5);
+        add(step, G - 1, 1.0);
+        for (int g = G - 2; g >= 0; g--) add(step, g, 0.5);
     }
-    canonicalize_1q(circ, n);
-    Schedule S;
-    e = schedule_circuit(circ, n, K, c, S);
-    if (!e.empty()) {
-        std::fprintf(stderr, "schedule: %s\n", e.c_str());
-        return 1;
+    // the segments of the call, as (circuit, repetitions)
+    std::vector<std::pair<Circuit, int64_t>> segs;
+    auto repeated = [&](const Circuit &one, int64_t count) {
+        if (reps > 1 && count >= reps) {
+            Circuit block;
+            for (int r = 0; r < reps; r++) {
+                // append one copy, rebasing its table indices
+                const int32_t np = (int32_t)block.phases.size(), nd = (int32_t)block.diags.size();
+                for (FlatOp op : one.ops) {
+                    if (op.kind == OK_PHASE) op.idx += np;
+                    else if (op.kind == OK_DIAG) op.idx += nd;
+                    block.ops.push_back(op);
+                }
+                block.phases.insert(block.phases.end(), one.phases.begin(), one.phases.end());
+                block.diags.insert(block.diags.end(), one.diags.begin(), one.diags.end());
+            }
+            segs.push_back({block, count / reps});
+            count %= reps;
+        }
+        if (count > 0) segs.push_back({one, count});
+    };
+    if (order == 1 || G == 1 || steps == 1) {
+        repeated(step, steps);
+    } else {
+        Circuit head, core, tail;
+        add(head, 0, 0.5);
+        for (int g = 1; g < G - 1; g++) {
+            add(core, g, 0.5);
+            add(tail, g, 0.5);
+        }
+        add(core, G - 1, 1.0);
+        add(tail, G - 1, 1.0);
+        for (int g = G - 2; g >= 1; g--) {
+            add(core, g, 0.5);
+            add(tail, g, 0.5);
+        }
+        add(core, 0, 1.0);
+        add(tail, 0, 0.5);
+        segs.push_back({head, 1});
+        repeated(core, steps - 1);
+        segs.push_back({tail, 1});
     }
-    Emulator em{n, S, psi};
-    for (int64_t s = 0; s < steps; s++)
-        for (const DevPass &P : S.passes) em.run_pass(P);
+    size_t passes = 0;
+    std::vector<Schedule> scheds(segs.size());
+    for (size_t i = 0; i < segs.size(); i++) {
+        if (!schedule(segs[i].first, n, K, c, scheds[i])) return 1;
+        Emulator em{n, scheds[i], psi};
+        for (int64_t r = 0; r < segs[i].second; r++)
+            for (const DevPass &P : scheds[i].passes) em.run_pass(P);
+        passes += scheds[i].passes.size() * (size_t)segs[i].second;
+    }
     f = std::fopen(argv[2], "wb");
     if (!f) return 2;
     std::fwrite(psi.data(), 16, psi.size(), f);
     std::fclose(f);
-    std::printf("passes %zu rounds %zu\n", S.passes.size(), S.rounds.size());
+    std::printf("passes %zu\n", passes);
     return 0;
 }

@@ -34,10 +34,10 @@ def emulator(tmp_path_factory):
     return exe
 
 
-def _run(exe, tmp_path, h, psi0, dt, steps, order, skip, K, c):
+def _run(exe, tmp_path, h, psi0, dt, steps, order, skip, K, c, reps=1):
     inp, out = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(inp, "wb") as f:
-        f.write(struct.pack("<iqiiiiqd", h.n, h.m, skip, K, c, order, steps, dt))
+        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c, order, reps, steps, dt))
         f.write(np.ascontiguousarray(h.x, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.z, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.c, dtype=np.float64).tobytes())
@@ -74,3 +74,22 @@ def test_schedule_matches_oracle(emulator, tmp_path, case, skip):
         ref = oracle.evolve(h, psi0, 0.05, 2, order, groups)
         err = np.linalg.norm(got - ref)
         assert err < 1e-10, (CASES[case][0], skip, order, K, err)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_blocks_at_the_default_tile_sizes(emulator, tmp_path, order):
+    """Calls of several steps as the library runs them -- blocks of 4 steps
+    (first order) or 4 merged cores (second order) scheduled as one circuit,
+    then the rest -- at the default tile sizes: K = 13 with 4 coalescing
+    qubits (complex64) and K = 12 with 3 (complex128)."""
+    rng = np.random.default_rng(800 + order)
+    cases = [heisenberg_lattice(4, 4), random_klocal(14, 50, rng, weights=(2, 3)),
+             jw_like(n=14, m=300, rng=rng)]
+    for h in cases:
+        groups = P.greedy_partition(h.x, h.z)
+        for K, c in ((13, 4), (12, 3)):
+            psi0 = _rand(rng, h.n)
+            got = _run(emulator, tmp_path, h, psi0, 0.03, 6, order, 2, K, c, reps=4)
+            ref = oracle.evolve(h, psi0, 0.03, 6, order, groups)
+            err = np.linalg.norm(got - ref)
+            assert err < 1e-10, (h.n, h.m, order, K, err)
