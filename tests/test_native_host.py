@@ -230,3 +230,38 @@ def test_argument_validation_of_the_other_entry_points(sd):
     assert lib.sd_prepare_batch(hs, ps, -1, N.SD_C64, 0.1, 1, 1) == N.SD_EINVAL
     assert lib.sd_prepare_batch(hs, ps, 70000, N.SD_C64, 0.1, 1, 1) == N.SD_EINVAL
     assert lib.sd_evolve_host(sim._h, None, None, N.SD_C64, 0.1, 1, 1, None) == N.SD_EINVAL
+
+
+def test_noalloc_argument_validation(sd):
+    """sd_expect_noalloc checks its arguments before touching a device: the
+    qubit range, null pointers, the dtype, the observable arrays, the fixed
+    limit of 4096 terms and mask bits at or above n; an empty observable
+    gives 0 without device work."""
+    from paper_2206_11664_gb300 import _native as N
+    lib = N.load()
+    fake = ctypes.c_void_p(0x1000)          # never dereferenced: every call below fails or returns early
+    out = ctypes.c_double(7.0)
+    m = 4097
+    ox = np.zeros(m, np.uint64)
+    oz = np.ones(m, np.uint64)
+    oc = np.ones(m)
+
+    def call(n, state, dtype, mo, x=ox, z=oz, c=oc, dst=ctypes.byref(out)):
+        return lib.sd_expect_noalloc(n, state, dtype, mo, x.ctypes.data_as(N.P_u64),
+                                     z.ctypes.data_as(N.P_u64), c.ctypes.data_as(N.P_dbl), dst, None)
+
+    assert call(0, fake, N.SD_C64, 1) == N.SD_EINVAL
+    assert call(41, fake, N.SD_C64, 1) == N.SD_EINVAL
+    assert call(4, None, N.SD_C64, 1) == N.SD_EINVAL
+    assert call(4, fake, N.SD_C64, 1, dst=None) == N.SD_EINVAL
+    assert call(4, fake, 7, 1) == N.SD_EINVAL
+    assert call(4, fake, N.SD_C64, -1) == N.SD_EINVAL
+    assert call(4, fake, N.SD_C64, m) == N.SD_EINVAL
+    assert b"4096" in lib.sd_last_error(None)
+    bad = oz.copy()
+    bad[0] = 1 << 4                         # a mask bit at n = 4
+    assert call(4, fake, N.SD_C128, 1, z=bad) == N.SD_EINVAL
+    nan = oc.copy()
+    nan[0] = float("nan")
+    assert call(4, fake, N.SD_C128, 1, c=nan) == N.SD_EINVAL
+    assert call(4, fake, N.SD_C128, 0) == N.SD_OK and out.value == 0.0
