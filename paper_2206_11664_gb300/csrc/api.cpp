@@ -864,11 +864,10 @@ sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_st
     const int G = (int)ctx->plan.groups.size();
     Circuit c = segment_circuit(ctx, order, (order == 2 && G > 1) ? 2 : 0, 0.01);
     canonicalize_1q(c, ctx->n);
-    Schedule S;
-    int K = default_tile_bits(ctx, dbl);
-    std::string e = schedule_circuit(c, ctx->n, K, dbl ? 3 : 4, S);
-    if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
-    out->tile_bits = K;
+    Schedule S;   // as sd_evolve schedules it (smaller tiles if a pass's terms need the room)
+    sd_status s = schedule_for(ctx, c, dbl, S);
+    if (s != SD_OK) return s;
+    out->tile_bits = S.K;
     out->passes_per_step = (int64_t)S.passes.size();
     out->rounds_per_step = (int64_t)S.rounds.size();
     out->diag_passes = S.diag_passes;

@@ -265,3 +265,22 @@ def test_noalloc_argument_validation(sd):
     nan[0] = float("nan")
     assert call(4, fake, N.SD_C128, 1, c=nan) == N.SD_EINVAL
     assert call(4, fake, N.SD_C128, 0) == N.SD_OK and out.value == 0.0
+
+
+def test_schedule_stats_report_the_tiles_sd_evolve_uses(sd):
+    """A diagonal group with thousands of distinct in-tile masks has more
+    term slots than fit beside a 2^13-amplitude complex64 tile in shared
+    memory, so the scheduler takes 2^12 tiles; the schedule statistics
+    report the tile size and pass count that sd_evolve runs."""
+    from workloads import Hamiltonian
+    rng = np.random.default_rng(3)
+    n, m = 16, 20000
+    z = rng.integers(1, 1 << n, size=m, dtype=np.uint64)
+    sim = sd.Simulator(n, np.zeros(m, dtype=np.uint64), z, rng.uniform(-1, 1, size=m)).plan()
+    st = sim.schedule_stats(sd.C64, 1)
+    assert st["tile_bits"] == 12
+    assert st["passes_per_step"] == sim.count_passes(sd.C64, 1, 1) == 1
+    h = heisenberg_lattice(4, 5)
+    small = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    assert small.schedule_stats(sd.C64, 1)["tile_bits"] == 13
+    assert small.schedule_stats(sd.C128, 1)["tile_bits"] == 12
