@@ -284,3 +284,58 @@ def test_schedule_stats_report_the_tiles_sd_evolve_uses(sd):
     small = sd.Simulator(h.n, h.x, h.z, h.c).plan()
     assert small.schedule_stats(sd.C64, 1)["tile_bits"] == 13
     assert small.schedule_stats(sd.C128, 1)["tile_bits"] == 12
+
+
+def _c_declarations():
+    """Function prototypes and struct typedefs of include/sd.h, comments removed."""
+    hdr = open(os.path.join(ROOT, "include", "sd.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", " ", hdr, flags=re.S)
+    funcs = {}
+    for ret, name, params in re.findall(r"(sd_status|const char \*|void)\s*(sd_[a-z_]+)\s*\(([^)]*)\)\s*;",
+                                        hdr):
+        funcs[name] = (ret.replace(" ", ""), [" ".join(p.split()) for p in params.split(",")])
+    structs = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(sd_[a-z_]+)\s*;", hdr, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if decl:
+                fields.append(decl)
+        structs[name] = fields
+    return funcs, structs
+
+
+def _ctype_of(decl):
+    """The ctypes type that marshals a C parameter declaration of sd.h."""
+    from paper_2206_11664_gb300 import _native as N
+    t = re.sub(r"\b[a-z_0-9]+$", "", decl).replace("const", "").replace(" ", "")
+    table = {"int": N.c_int, "int64_t": N.c_i64, "double": N.c_dbl, "sd_dtype": N.c_int,
+             "void*": N.c_vp, "sd_ctx*": N.c_vp, "sd_ctx**": ctypes.POINTER(N.c_vp),
+             "uint64_t*": N.P_u64, "double*": N.P_dbl, "char**": ctypes.POINTER(ctypes.c_char_p),
+             "sd_plan_opts*": ctypes.POINTER(N.PlanOpts), "sd_plan_view*": ctypes.POINTER(N.PlanView),
+             "sd_schedule_stats*": ctypes.POINTER(N.ScheduleStats), "int*": ctypes.POINTER(N.c_int),
+             "int64_t*": ctypes.POINTER(N.c_i64), "void**": ctypes.POINTER(N.c_vp),
+             "sd_ctx**const": ctypes.POINTER(N.c_vp)}
+    return table[t]
+
+
+def test_binding_matches_the_header():
+    """Every prototype of include/sd.h is bound with the same number and kind
+    of arguments and the same result type, and the binding's structures have
+    the header's fields in the header's order."""
+    from paper_2206_11664_gb300 import _native as N
+    funcs, structs = _c_declarations()
+    assert set(funcs) == set(N.SIGNATURES)
+    results = {"sd_status": N.c_int, "constchar*": ctypes.c_char_p, "void": None}
+    for name, (ret, params) in funcs.items():
+        res, args = N.SIGNATURES[name]
+        assert res is results[ret], name
+        assert len(args) == len(params), name
+        for decl, a in zip(params, args):
+            device_ptr = "*" in decl and decl.split()[-1].lstrip("*").startswith("d_")
+            # device addresses (d_...) are passed as plain addresses
+            assert _ctype_of(decl) == a or (device_ptr and a is N.c_vp), (name, decl)
+    for cname, pyname in (("sd_plan_opts", "PlanOpts"), ("sd_plan_view", "PlanView"),
+                          ("sd_schedule_stats", "ScheduleStats")):
+        header_fields = [re.sub(r"\[.*\]", "", d).split()[-1].lstrip("*") for d in structs[cname]]
+        assert header_fields == [f[0] for f in getattr(N, pyname)._fields_], cname
