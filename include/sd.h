@@ -57,7 +57,8 @@ typedef enum {
     SD_ENOMEM = 2,     /* host or device allocation failed */
     SD_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
     SD_ENOPLAN = 4,    /* sd_plan has not been called on this context */
-    SD_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    SD_ETIMEOUT = 5,   /* reserved: no kernel of this library waits on another
+                          block, kernel or device, so no call returns it */
     SD_EINTERNAL = 6   /* a planner invariant failed (e.g. a term not diagonal) */
 } sd_status;
 
