@@ -339,3 +339,21 @@ def test_binding_matches_the_header():
                           ("sd_schedule_stats", "ScheduleStats")):
         header_fields = [re.sub(r"\[.*\]", "", d).split()[-1].lstrip("*") for d in structs[cname]]
         assert header_fields == [f[0] for f in getattr(N, pyname)._fields_], cname
+
+
+def test_pass_counts_of_the_benchmark_steps(sd):
+    """Tile passes (state sweeps through HBM) of the benchmark workloads, as
+    the scheduler plans them on the host; the benchmark's launch count and
+    bytes come from these numbers.  5x6 Heisenberg: 7 passes for one step,
+    25 for a block of 4 steps (6.25 per step); 6x6 minus corners (n = 32):
+    10 and 37.  A change here changes the measured roofline figures."""
+    for (rows, cols, corners), one, four in (((5, 6, False), 7, 25), ((6, 6, True), 10, 37)):
+        h = heisenberg_lattice(rows, cols, drop_corners=corners)
+        sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+        for code in (sd.C64, sd.C128):
+            st = sim.schedule_stats(code, 1)
+            assert st["passes_per_step"] == one and st["diag_passes"] == 3
+            assert sim.count_passes(code, 1, 1) == one
+            assert sim.count_passes(code, 1, 20) == 5 * four
+            assert sim.count_passes(code, 1, 1000) == 250 * four
+            assert sim.count_passes(code, 1, 6) == four + 2 * one
