@@ -807,7 +807,6 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     ctx->jit_opt = jit;
     ctx->planned = true;
     // plan view
-    const int n = ctx->n;
     ctx->v_goff.assign(1, 0);
     ctx->v_gterms.clear();
     ctx->v_masks.clear();
@@ -832,7 +831,6 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
         ctx->v_cols.insert(ctx->v_cols.end(), g.cnot_cols.begin(), g.cnot_cols.end());
         ctx->v_icols.insert(ctx->v_icols.end(), g.cnot_inv_cols.begin(), g.cnot_inv_cols.end());
     }
-    (void)n;
     return SD_OK;
 }
 
