@@ -25,7 +25,11 @@
 // merged) in blocks of `reps` and single cores, and closes with the last
 // core, whose group 1 takes a half step.
 //
-// Usage: schedule_emulator <input> <output>.
+// It also counts, for every round, whether the warps' accesses to the
+// shared-memory exchange are free of bank conflicts (see bank_stats).
+//
+// Usage: schedule_emulator <input> <output>, or <input> - to schedule only
+// (the input then ends before the state, and nothing is executed).
 // The input is binary, in this order: int32 n, int64 m, int32 skip_rule,
 // int32 K, int32 c, int32 order, int32 reps, int64 steps, float64 dt,
 // uint64 x[m], uint64 z[m], float64 coeffs[m], complex128 psi[2^n]. The
@@ -169,6 +173,54 @@ struct Emulator {
 
 }  // namespace
 
+// Rank over GF(2) of the low c bits (the bank-selecting bits of an
+// amplitude's swizzled shared-memory index) of a set of columns.
+int bank_rank(std::vector<uint32_t> cols, int c) {
+    const uint32_t mask = (1u << c) - 1u;
+    int r = 0;
+    for (int b = c - 1; b >= 0; b--) {
+        size_t i = r;
+        while (i < cols.size() && !((cols[i] & mask) >> b & 1)) i++;
+        if (i == cols.size()) continue;
+        std::swap(cols[r], cols[i]);
+        for (size_t j = 0; j < cols.size(); j++)
+            if ((int)j != r && ((cols[j] & mask) >> b & 1)) cols[j] ^= cols[r];
+        r++;
+    }
+    return r;
+}
+
+// Shared-memory bank use of a schedule's exchanges.  A warp's access to the
+// exchange buffer varies the swizzled index over the XOR combinations of the
+// columns of its 5 lane positions; it is free of bank conflicts when the low c
+// bits of those columns have rank c.  Counted: rounds whose lane columns fall
+// short, and permutation rounds whose permuted write columns fall short.
+struct BankStats {
+    long rounds = 0, short_lanes = 0, perm_rounds = 0, short_perm = 0;
+};
+
+void bank_stats(const Schedule &S, BankStats &b) {
+    const int c = S.c;
+    for (const DevRound &R : S.rounds) {
+        std::vector<uint32_t> cols;
+        for (int i = 0; i < 5; i++) cols.push_back(swizzle_col(R.lane_pos[i], c));
+        b.rounds++;
+        if (bank_rank(cols, c) < c) b.short_lanes++;
+        if (R.perm >= 0) {
+            const DevPerm &pm = S.perms[R.perm];
+            std::vector<uint32_t> pc;
+            for (int i = 0; i < 5; i++) {
+                uint32_t t = pm.col[R.lane_pos[i]], sw = 0;
+                for (int p = 0; p < S.K; p++)
+                    if ((t >> p) & 1) sw ^= swizzle_col(p, c);
+                pc.push_back(sw);
+            }
+            b.perm_rounds++;
+            if (bank_rank(pc, c) < c) b.short_perm++;
+        }
+    }
+}
+
 // Schedules a circuit (one-qubit runs canonicalised first).
 bool schedule(Circuit circ, int n, int K, int c, Schedule &S) {
     canonicalize_1q(circ, n);
@@ -178,7 +230,9 @@ bool schedule(Circuit circ, int n, int K, int c, Schedule &S) {
 }
 
 int main(int argc, char **argv) {
+    // "-" as the output: schedule only (no state in the input, nothing executed)
     if (argc != 3) return 2;
+    const bool run = std::string(argv[2]) != "-";
     FILE *f = std::fopen(argv[1], "rb");
     if (!f) return 2;
     int32_t n, skip, K, c, order, reps;
@@ -190,7 +244,7 @@ int main(int argc, char **argv) {
     ok = ok && reps >= 1;
     std::vector<uint64_t> x(m), z(m);
     std::vector<double> coef(m);
-    std::vector<cd> psi((size_t)1 << n);
+    std::vector<cd> psi(run ? (size_t)1 << n : 0);
     ok = ok && std::fread(x.data(), 8, m, f) == (size_t)m && std::fread(z.data(), 8, m, f) == (size_t)m &&
          std::fread(coef.data(), 8, m, f) == (size_t)m && std::fread(psi.data(), 16, psi.size(), f) == psi.size();
     std::fclose(f);
@@ -255,18 +309,24 @@ int main(int argc, char **argv) {
         segs.push_back({tail, 1});
     }
     size_t passes = 0;
+    BankStats banks;
     std::vector<Schedule> scheds(segs.size());
     for (size_t i = 0; i < segs.size(); i++) {
         if (!schedule(segs[i].first, n, K, c, scheds[i])) return 1;
+        bank_stats(scheds[i], banks);
         Emulator em{n, scheds[i], psi};
-        for (int64_t r = 0; r < segs[i].second; r++)
-            for (const DevPass &P : scheds[i].passes) em.run_pass(P);
+        if (run)
+            for (int64_t r = 0; r < segs[i].second; r++)
+                for (const DevPass &P : scheds[i].passes) em.run_pass(P);
         passes += scheds[i].passes.size() * (size_t)segs[i].second;
     }
-    f = std::fopen(argv[2], "wb");
-    if (!f) return 2;
-    std::fwrite(psi.data(), 16, psi.size(), f);
-    std::fclose(f);
+    if (run) {
+        f = std::fopen(argv[2], "wb");
+        if (!f) return 2;
+        std::fwrite(psi.data(), 16, psi.size(), f);
+        std::fclose(f);
+    }
     std::printf("passes %zu\n", passes);
+    std::printf("banks %ld %ld %ld %ld\n", banks.rounds, banks.short_lanes, banks.perm_rounds, banks.short_perm);
     return 0;
 }

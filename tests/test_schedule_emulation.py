@@ -93,3 +93,33 @@ def test_blocks_at_the_default_tile_sizes(emulator, tmp_path, order):
             ref = oracle.evolve(h, psi0, 0.03, 6, order, groups)
             err = np.linalg.norm(got - ref)
             assert err < 1e-10, (h.n, h.m, order, K, err)
+
+
+def _schedule_only(exe, tmp_path, h, order, K, c, steps, reps):
+    """Passes of a call and the bank statistics of its rounds, without a state."""
+    inp = tmp_path / "sched.bin"
+    with open(inp, "wb") as f:
+        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, 2, K, c, order, reps, steps, 0.02))
+        f.write(np.ascontiguousarray(h.x, dtype=np.uint64).tobytes())
+        f.write(np.ascontiguousarray(h.z, dtype=np.uint64).tobytes())
+        f.write(np.ascontiguousarray(h.c, dtype=np.float64).tobytes())
+    r = subprocess.run([exe, str(inp), "-"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = dict(line.split(None, 1) for line in r.stdout.strip().splitlines())
+    rounds, short_lanes, perm_rounds, short_perm = (int(v) for v in lines["banks"].split())
+    return int(lines["passes"]), rounds, short_lanes, perm_rounds, short_perm
+
+
+def test_benchmark_rounds_are_free_of_bank_conflicts(emulator, tmp_path):
+    """The benchmark calls (20 first-order steps of the 5x6 and 6x6-minus-
+    corners Heisenberg models, both tile sizes): the call splits into the
+    passes the library counts, and in every round the 5 lane positions' swizzle
+    columns span the c bank-selecting bits, so each warp access to the
+    shared-memory exchange touches every bank equally (no conflicts); these
+    steps need no tile permutations."""
+    for (rows, cols, corners), passes in (((5, 6, False), 125), ((6, 6, True), 185)):
+        h = heisenberg_lattice(rows, cols, drop_corners=corners)
+        for K, c in ((13, 4), (12, 3)):
+            got, rounds, short_lanes, perm_rounds, _ = _schedule_only(emulator, tmp_path, h, 1, K, c, 20, 4)
+            assert got == passes
+            assert rounds > 0 and short_lanes == 0 and perm_rounds == 0
