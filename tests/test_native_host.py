@@ -357,3 +357,16 @@ def test_pass_counts_of_the_benchmark_steps(sd):
             assert sim.count_passes(code, 1, 20) == 5 * four
             assert sim.count_passes(code, 1, 1000) == 250 * four
             assert sim.count_passes(code, 1, 6) == four + 2 * one
+
+
+def test_precompile_the_benchmark_programs(sd, tmp_path, monkeypatch):
+    """The exact kernels of the benchmark's timed calls (5x6 Heisenberg,
+    n = 30, 20 first-order steps: a 25-pass block program, complex64 and
+    complex128) are generated and compile with NVRTC for sm_103a on the host
+    alone."""
+    monkeypatch.setenv("SD_JIT_CACHE", str(tmp_path))
+    h = heisenberg_lattice(5, 6)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    for code in (sd.C64, sd.C128):
+        assert sim.precompile(code, 20, 1) == 3      # 25 passes in NVRTC programs of 12
+        assert sim.precompile(code, 20, 1) == 0      # then all cached
