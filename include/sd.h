@@ -125,7 +125,8 @@ typedef struct {
 sd_status sd_create(int n, int64_t m, const uint64_t *xmask, const uint64_t *zmask,
                     const double *coeffs, sd_ctx **out);
 
-/* Same, from text strings of length n over {I,X,Y,Z} (character q = qubit q). */
+/* Same, from text strings of length n over {I,X,Y,Z} (character q = qubit q;
+ * lower-case letters are accepted; any other character gives SD_EINVAL). */
 sd_status sd_create_str(int n, int64_t m, const char *const *paulis, const double *coeffs,
                         sd_ctx **out);
 

@@ -84,7 +84,10 @@ class Simulator:
     def from_strings(cls, strings, coeffs):
         """Terms as text over {I,X,Y,Z}, character q = qubit q (sd_create_str)."""
         self = cls.__new__(cls)
+        self._h = None
         self._lib = N.load()
+        if len(strings) == 0:
+            raise ValueError("need at least one Pauli string")
         self.n = len(strings[0])
         self.m = len(strings)
         c = _f64(coeffs)

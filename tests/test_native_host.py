@@ -370,3 +370,17 @@ def test_precompile_the_benchmark_programs(sd, tmp_path, monkeypatch):
     for code in (sd.C64, sd.C128):
         assert sim.precompile(code, 20, 1) == 3      # 25 passes in NVRTC programs of 12
         assert sim.precompile(code, 20, 1) == 0      # then all cached
+
+
+def test_from_strings_arguments(sd):
+    """Text input: lower case is accepted and gives the same plan; an empty
+    list, a wrong length or a character outside IXYZ is refused."""
+    a = sd.Simulator.from_strings(["XXI", "iyy", "ZIZ"], [1.0, 0.5, 0.25]).plan().plan_view()
+    b = sd.Simulator.from_strings(["XXI", "IYY", "ZIZ"], [1.0, 0.5, 0.25]).plan().plan_view()
+    assert a["n_groups"] == b["n_groups"] and a["masks"].tolist() == b["masks"].tolist()
+    with pytest.raises(ValueError):
+        sd.Simulator.from_strings([], [])
+    with pytest.raises(sd.SDError):
+        sd.Simulator.from_strings(["XX", "XYZ"], [1.0, 1.0])
+    with pytest.raises(sd.SDError):
+        sd.Simulator.from_strings(["XQ"], [1.0])
