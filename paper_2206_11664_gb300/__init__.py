@@ -38,6 +38,15 @@ def _ptr(a, t):
     return a.ctypes.data_as(t)
 
 
+def _obs(obs):
+    """(x, z, c) arrays of a Pauli-sum observable, checked for equal length
+    (the library reads len(c) entries of each)."""
+    ox, oz, oc = _u64(obs[0]), _u64(obs[1]), _f64(obs[2])
+    if not (oc.ndim == 1 and ox.shape == oz.shape == oc.shape):
+        raise ValueError("observable arrays x, z, c must be 1-D and of equal length")
+    return ox, oz, oc
+
+
 def _dtype_of(state, n=None):
     import torch
     if not isinstance(state, torch.Tensor) or not state.is_cuda:
@@ -224,7 +233,7 @@ class Simulator:
         import torch
         if trace.dtype != torch.float64 or not trace.is_cuda or trace.numel() < steps:
             raise ValueError("trace must be a CUDA float64 tensor with >= steps entries")
-        ox, oz, oc = _u64(obs[0]), _u64(obs[1]), _f64(obs[2])
+        ox, oz, oc = _obs(obs)
         self._check(self._lib.sd_evolve_observe(
             self._h, ctypes.c_void_p(state.data_ptr()), _dtype_of(state, self.n), float(dt), int(steps),
             int(order), len(oc), _ptr(ox, N.P_u64), _ptr(oz, N.P_u64), _ptr(oc, N.P_dbl),
@@ -232,7 +241,7 @@ class Simulator:
         return trace
 
     def expect(self, state, obs, stream=None):
-        ox, oz, oc = _u64(obs[0]), _u64(obs[1]), _f64(obs[2])
+        ox, oz, oc = _obs(obs)
         out = ctypes.c_double()
         self._check(self._lib.sd_expect(self._h, ctypes.c_void_p(state.data_ptr()), _dtype_of(state, self.n),
                                         len(oc), _ptr(ox, N.P_u64), _ptr(oz, N.P_u64),
@@ -241,7 +250,7 @@ class Simulator:
 
     def grad(self, state0, dt, steps, obs, order=1, stream=None):
         """(f, df/dc) for f = <psi_T|O|psi_T>, psi_T = evolve(state0); state0 unchanged."""
-        ox, oz, oc = _u64(obs[0]), _u64(obs[1]), _f64(obs[2])
+        ox, oz, oc = _obs(obs)
         g = np.zeros(self.m, np.float64)
         f = ctypes.c_double()
         self._check(self._lib.sd_grad(self._h, ctypes.c_void_p(state0.data_ptr()), _dtype_of(state0, self.n),

@@ -384,3 +384,17 @@ def test_from_strings_arguments(sd):
         sd.Simulator.from_strings(["XX", "XYZ"], [1.0, 1.0])
     with pytest.raises(sd.SDError):
         sd.Simulator.from_strings(["XQ"], [1.0])
+
+
+def test_observable_arrays_must_match(sd):
+    """The binding refuses observables whose x, z and c arrays differ in
+    length before any call into the library (which reads len(c) of each)."""
+    h = heisenberg_lattice(3, 3)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    bad = (np.zeros(2, np.uint64), np.ones(3, np.uint64), np.ones(3))
+    with pytest.raises(ValueError):
+        sim.expect(None, bad)
+    with pytest.raises(ValueError):
+        sim.grad(None, 0.1, 1, bad)
+    with pytest.raises(ValueError):
+        sim.expect(None, (np.zeros((1, 3), np.uint64), np.ones((1, 3), np.uint64), np.ones((1, 3))))
