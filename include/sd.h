@@ -236,7 +236,9 @@ sd_status sd_expect(sd_ctx *ctx, const void *d_state, sd_dtype dtype, int64_t mo
  * order) of the evolution sd_evolve(d_state0, dt, steps, order) by an
  * adjoint sweep that undoes each group exponential (no checkpoints).
  * d_state0 is not modified; two device work vectors of the state's size are
- * allocated by the library and kept for later calls. */
+ * allocated by the library and kept for later calls.  Needs n >= 4 (the
+ * per-term sums run over 16-amplitude register groups); smaller n gives
+ * SD_EINVAL.  Synchronises the stream. */
 sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt,
                   int64_t steps, int order, int64_t mo, const uint64_t *ox,
                   const uint64_t *oz, const double *oc, double *value_out,
