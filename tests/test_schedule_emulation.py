@@ -95,11 +95,11 @@ def test_blocks_at_the_default_tile_sizes(emulator, tmp_path, order):
             assert err < 1e-10, (h.n, h.m, order, K, err)
 
 
-def _schedule_only(exe, tmp_path, h, order, K, c, steps, reps):
+def _schedule_only(exe, tmp_path, h, order, K, c, steps, reps, skip=2):
     """Passes of a call and the bank statistics of its rounds, without a state."""
     inp = tmp_path / "sched.bin"
     with open(inp, "wb") as f:
-        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, 2, K, c, order, reps, steps, 0.02))
+        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c, order, reps, steps, 0.02))
         f.write(np.ascontiguousarray(h.x, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.z, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.c, dtype=np.float64).tobytes())
@@ -123,3 +123,20 @@ def test_benchmark_rounds_are_free_of_bank_conflicts(emulator, tmp_path):
             got, rounds, short_lanes, perm_rounds, _ = _schedule_only(emulator, tmp_path, h, 1, K, c, 20, 4)
             assert got == passes
             assert rounds > 0 and short_lanes == 0 and perm_rounds == 0
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_blocks_with_cnot_permutations(emulator, tmp_path, order):
+    """Blocks at the default tile sizes when every qubit goes through the
+    synthesis steps (skip rule 0): the CNOT layers become tile permutations
+    inside the block programs."""
+    rng = np.random.default_rng(820 + order)
+    h = random_klocal(14, 40, rng, weights=(2, 3, 4))
+    groups = P.greedy_partition(h.x, h.z)
+    for K, c in ((13, 4), (12, 3)):
+        psi0 = _rand(rng, h.n)
+        got = _run(emulator, tmp_path, h, psi0, 0.04, 5, order, 0, K, c, reps=4)
+        ref = oracle.evolve(h, psi0, 0.04, 5, order, groups)
+        assert np.linalg.norm(got - ref) < 1e-10, (order, K)
+    _, rounds, _, perm_rounds, _ = _schedule_only(emulator, tmp_path, h, order, 13, 4, 5, 4, skip=0)
+    assert perm_rounds > 0
