@@ -89,6 +89,16 @@ def test_planner_bit_exact_random(sd, rule):
         _compare(sd, h, rule)
 
 
+def test_planner_bit_exact_where_completion_uses_the_complement(sd):
+    """Groups whose generators no single-qubit Pauli can complete (every
+    qubit carries both X and Z), so that both planners must take rows from
+    the symplectic complement; embedded in larger registers as well."""
+    for texts in (["XXXX", "ZZZZ", "YYYY"], ["XXXXII", "ZZZZII", "IIIIXX"],
+                  ["IXXXXI", "IZZZZI", "XIIIIZ", "ZIIIIX"]):
+        for rule in (0, 1, 2):
+            _compare(sd, from_strings(texts, np.linspace(0.3, 1.1, len(texts))), rule)
+
+
 def test_argument_validation(sd):
     from paper_2206_11664_gb300 import _native as N
     lib = N.load()

@@ -198,6 +198,12 @@ PLANNER_MUTANTS = [
     ("first fit ignoring anticommutation",
      "            if not anti.any():",
      "            if True:"),
+    ("symplectic complement built from (x, z) instead of (z, x)",
+     "        cons.append(z | (x << n))\n",
+     "        cons.append(x | (z << n))\n"),
+    ("complement basis vector without its pivot entries",
+     "            if _bit(M[i], f):\n                v |= 1 << pc\n",
+     "            pass\n"),
     ("CNOT map inverse taken in the forward order",
      "return run(cn), run(list(reversed(cn)))",
      "return run(cn), run(cn)"),

@@ -327,3 +327,96 @@ def test_largest_first_and_magnitude_orders():
     assert P.partition(x, z, P.BY_MAGNITUDE, c) == [[0, 1, 2], [3]]
     c2 = np.array([0.1, 0.2, 0.3, 5.0])
     assert P.partition(x, z, P.BY_MAGNITUDE, c2) == [[3], [0, 1, 2]]
+
+
+# ---------------------------------------------------------------- completion branch
+
+def _sym(a, b, n):
+    m = (1 << n) - 1
+    return (((a & m) & (b >> n)) ^ ((a >> n) & (b & m))).bit_count() & 1
+
+
+def _span(rows):
+    out = {0}
+    for r in rows:
+        out |= {v ^ r for v in out}
+    return out
+
+
+@pytest.mark.parametrize("rows_text", [["XXXX", "ZZZZ"], ["XXXX"], ["XYZI", "ZXYI"], ["XXII", "ZZII", "IIXX"]])
+def test_symplectic_complement_basis_is_the_complement(rows_text):
+    """The basis returned for the symplectic complement of independent rows S
+    must be a basis of {v : <v, s> = 0 for every s in S}: every vector is
+    orthogonal to S, the vectors are independent, there are 2n - |S| of them,
+    and (brute force over all 4^n vectors) their span is the whole set."""
+    n = len(rows_text[0])
+    rows = []
+    for t in rows_text:
+        x, z = pauli_to_masks(t)
+        rows.append(x | (z << n))
+    assert P.gf2_rank(rows) == len(rows)
+    basis = P.symplectic_complement_basis(rows, n)
+    assert len(basis) == 2 * n - len(rows)
+    assert P.gf2_rank(basis) == len(basis)
+    for v in basis:
+        assert all(_sym(v, s, n) == 0 for s in rows)
+    brute = {v for v in range(1 << (2 * n)) if all(_sym(v, s, n) == 0 for s in rows)}
+    assert _span(basis) == brute
+
+
+def test_completion_needs_the_complement_branch():
+    """{XXXX, ZZZZ} commute (four anticommuting positions), but every qubit
+    carries both X and Z, so no single-qubit Z, X or Y commutes with both:
+    the completion must take its rows from the symplectic complement.  The
+    completed set must hold the original rows, have n independent mutually
+    commuting rows, and the synthesis must then diagonalise the group
+    (dense check of C P C^dag)."""
+    n = 4
+    rows = []
+    for t in ("XXXX", "ZZZZ"):
+        x, z = pauli_to_masks(t)
+        rows.append(x | (z << n))
+    for q in range(n):
+        for x, z in ((0, 1 << q), (1 << q, 0), (1 << q, 1 << q)):
+            assert any(_sym(x | (z << n), s, n) for s in rows)
+    done = P.complete_generators(rows, n)
+    assert done[:2] == rows and len(done) == n
+    assert P.gf2_rank(done) == n
+    assert all(_sym(a, b, n) == 0 for a in done for b in done)
+    # the group itself, with products in it, through the whole synthesis
+    texts = ["XXXX", "ZZZZ", "YYYY"]
+    xs, zs = zip(*(pauli_to_masks(t) for t in texts))
+    for rule in (P.SKIP_NONE, P.SKIP_PAPER, P.SKIP_Y):
+        gates, masks, signs = P.synthesize_group(n, list(xs), list(zs), skip_rule=rule)
+        C = D.circuit(n, gates)
+        for a, b, mk, sg in zip(xs, zs, masks, signs):
+            lhs = C @ D.pauli(n, a, b) @ C.conj().T
+            assert np.allclose(lhs, (-1) ** sg * D.pauli(n, 0, mk))
+
+
+def test_completion_branch_on_larger_groups():
+    """Groups where single-qubit candidates run out before n rows: the
+    complement branch fills the rest, and every completed set is a maximal
+    isotropic set containing the original generators."""
+    rng = np.random.default_rng(12)
+    hits = 0
+    for _ in range(60):
+        n = int(rng.integers(4, 8))
+        # pairs of strings with X and Z on the same support commute when the support is even
+        k = int(rng.integers(1, n // 2 + 1))
+        rows = []
+        for _ in range(k):
+            supp = rng.choice(n, size=2 * int(rng.integers(1, n // 2 + 1)), replace=False)
+            x = sum(1 << int(q) for q in supp)
+            cand = [x, x << n]
+            for v in cand:
+                if all(_sym(v, s, n) == 0 for s in rows) and P.gf2_rank(rows + [v]) == len(rows) + 1:
+                    rows.append(v)
+        singles_left = [v for q in range(n) for v in (1 << (q + n), 1 << q, (1 << q) | (1 << (q + n)))
+                        if all(_sym(v, s, n) == 0 for s in rows) and P.gf2_rank(rows + [v]) > len(rows)]
+        done = P.complete_generators(rows, n)
+        assert done[:len(rows)] == rows and len(done) == n
+        assert P.gf2_rank(done) == n
+        assert all(_sym(a, b, n) == 0 for a in done for b in done)
+        hits += not singles_left
+    assert hits > 0
