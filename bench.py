@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--pauli-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip per-Pauli / c128 / e2e legs")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the 2-step comparison of both precisions with the CPU oracle")
     ap.add_argument("--workload", default="heisenberg30",
                     choices=["heisenberg30", "heisenberg32", "tfim10", "batch", "jw26", "grad24",
                              "tfim_fc", "syk", "sweep"],
@@ -172,76 +174,129 @@ DT = 0.02
 TRAFFIC_PER_LAUNCH = {28: 4.235e9, 30: 16.94e9}
 
 
-def cpu_oracle_sample(h, neel, budget_s=15.0, psi=None, threads=None):
-    """Oracle (one rotation at a time, complex128, OpenMP on the host cores)
-    on a bounded sample of one Trotter step: the first k rotations of the
-    grouped order, timed and scaled to the step's m rotations.  psi (the
-    2^n host state) is reused when given; threads (default: all cores)
-    sets the OpenMP thread count for this sample only."""
-    import oracle
+def oracle_sample(h, per_group):
+    """The rotations of one grouped Trotter step that a bounded CPU sample
+    times: `per_group` of them, evenly spaced, from every group (so that
+    non-diagonal and diagonal rotations are both represented), and the
+    number of rotations in the whole step."""
     from oracle import planner as P
-    if threads is not None:
-        all_threads = oracle.num_threads()
-        oracle.set_threads(threads)
-        try:
-            return cpu_oracle_sample(h, neel, budget_s, psi)
-        finally:
-            oracle.set_threads(all_threads)
     groups = P.greedy_partition(h.x, h.z)
-    seq = [j for g in groups for j in g]
-    if psi is None:
-        psi = np.zeros(1 << h.n, dtype=np.complex128)
-        psi[neel] = 1.0
-    t0 = time.perf_counter()
-    j = seq[0]
-    psi = _oracle_rot_inplace(oracle, psi, h, j)
-    t1 = time.perf_counter() - t0
-    k = int(max(1, min(len(seq) - 1, budget_s / max(t1, 1e-6))))
-    t0 = time.perf_counter()
-    for j in seq[1:1 + k]:
-        psi = _oracle_rot_inplace(oracle, psi, h, j)
-    tk = time.perf_counter() - t0
-    per_rot = tk / k
-    return {"value": 1.0 / (per_rot * len(seq)), "unit": "steps/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{k} of the {len(seq)} rotations of one Trotter step (grouped order) at n={h.n}, "
-                      f"complex128, {tk:.1f} s, scaled to a full step"}
+    picks = []
+    for g in groups:
+        k = min(per_group, len(g))
+        picks += [g[(i * len(g)) // k] for i in range(k)]
+    return picks, sum(len(g) for g in groups)
 
 
-def _oracle_rot_inplace(oracle, psi, h, j):
+def time_oracle_rotations(h, psi, picks):
+    """Wall seconds of the oracle applying the picked rotations, one at a
+    time, to the 2^n complex128 host state psi (in place)."""
     import ctypes
+    import oracle
     lib = oracle.lib()
-    lib.oracle_apply_rotation(h.n, psi.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                              int(h.x[j]), int(h.z[j]), float(h.c[j] * DT))
-    return psi
+    ptr = psi.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    t0 = time.perf_counter()
+    for j in picks:
+        lib.oracle_apply_rotation(h.n, ptr, int(h.x[j]), int(h.z[j]), float(h.c[j] * DT))
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_sample(h, psi, per_group, threads=None):
+    """Oracle (one rotation at a time, complex128, OpenMP on the host cores)
+    on a bounded sample of one Trotter step (oracle_sample), scaled to whole
+    steps: value = (sampled rotations / rotations per step) / seconds.
+    threads (default: all cores) sets the OpenMP thread count for this
+    sample only."""
+    import oracle
+    all_threads = oracle.num_threads()
+    if threads is not None:
+        oracle.set_threads(threads)
+    try:
+        picks, m = oracle_sample(h, per_group)
+        time_oracle_rotations(h, psi, picks[:1])          # first touch, thread start
+        t = time_oracle_rotations(h, psi, picks)
+        cores = oracle.num_threads()
+    finally:
+        oracle.set_threads(all_threads)
+    return {"value": len(picks) / m / t, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(picks)} of the {m} rotations of one Trotter step at n={h.n} "
+                      f"({per_group} evenly spaced from each group), complex128, {t:.1f} s, "
+                      f"scaled to a whole step"}
+
+
+REFERENCE_PER_GROUP = 7   # rotations per group in one step of the reference arm
 
 
 def run_reference(args):
+    """The oracle as the reference arm.  A whole Trotter step of the oracle
+    at n = 30 takes about half a minute of the host's cores, so each of the
+    arm's steps is a bounded sample of one: REFERENCE_PER_GROUP rotations
+    from every group.  ms_per_step is the measured wall time of one such
+    sample step; value scales it to whole Trotter steps per second."""
     # The oracle runs on rank 0's host cores only; the other ranks have no
     # work and exit at once, so no process group is needed.
     if int(os.environ.get("RANK", "0")) != 0:
         return
+    import oracle
     h, neel, name = workload(args.qubits)
-    vals = []
-    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    info = None
+    picks, m = oracle_sample(h, REFERENCE_PER_GROUP)
     psi = np.zeros(1 << h.n, dtype=np.complex128)
     psi[neel] = 1.0
+    times = []
     for i in range(args.warmup + args.steps):
-        info = cpu_oracle_sample(h, neel, budget_s=budget, psi=psi)
+        t = time_oracle_rotations(h, psi, picks)
         if i >= args.warmup:
-            vals.append(info["value"])
-    v = float(np.mean(vals))
+            times.append(t)
+    t = float(np.mean(times))
+    frac = len(picks) / m
+    v = frac / t
+    sample = (f"one step = {len(picks)} of the {m} rotations of one Trotter step at n={h.n} "
+              f"({REFERENCE_PER_GROUP} evenly spaced from each group), complex128; value = "
+              f"{len(picks)}/{m} Trotter steps / measured seconds per step")
     out = {"metric": METRIC, "value": v, "unit": "steps/s", "impl": "reference",
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+           "trotter_steps_per_step": frac,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
            "data": "synthetic", "config": {"workload": name, "n": h.n, "terms": h.m, "dt": DT,
                                             "order": 1, "initial": "neel"},
-           "cpu_baseline": {"value": v, "unit": "steps/s", "kind": "oracle", "cores": info["cores"],
-                            "sample": info["sample"]},
+           "cpu_baseline": {"value": v, "unit": "steps/s", "kind": "oracle",
+                            "cores": oracle.num_threads(), "sample": sample},
            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def oracle_accuracy(sim, h, neel, dev, steps=2):
+    """||psi_gpu - psi_oracle||_2 after `steps` first-order steps from the
+    Neel state, for the complex64 and complex128 grouped paths, against the
+    oracle (complex128, one rotation at a time) run on the host cores.  The
+    comparison runs in chunks, so the host holds the oracle's state and one
+    chunk of the GPU's."""
+    import torch
+    import oracle
+    import paper_2206_11664_gb300 as sd
+    N = 1 << h.n
+    psi0 = np.zeros(N, dtype=np.complex128)
+    psi0[neel] = 1.0
+    t0 = time.perf_counter()
+    ref = oracle.evolve(h, psi0, DT, steps, 1)
+    t_oracle = time.perf_counter() - t0
+    del psi0
+    out = {"steps": steps, "oracle_s": t_oracle, "oracle_cores": oracle.num_threads()}
+    chunk = 1 << 26
+    for cdt, key in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+        s = torch.zeros(N, dtype=cdt, device=dev)
+        s[neel] = 1.0
+        sim.evolve(s, DT, steps, 1)
+        acc = 0.0
+        for a in range(0, N, chunk):
+            g = s[a:a + chunk].to(torch.complex128).cpu().numpy()
+            acc += float(np.sum(np.abs(g - ref[a:a + chunk]) ** 2))
+        out["l2_" + key] = acc ** 0.5
+        del s
+        torch.cuda.empty_cache()
+    out["tolerance"] = {"c64": 1e-4, "c128": 1e-10}
+    return out
 
 
 def main():
@@ -391,12 +446,15 @@ def main():
         # all host cores, then one core, on the same host state
         psi = np.zeros(N, dtype=np.complex128)
         psi[neel] = 1.0
-        cb = cpu_oracle_sample(h, neel, budget_s=12.0, psi=psi)
-        one = cpu_oracle_sample(h, neel, budget_s=8.0, psi=psi, threads=1)
+        cb = cpu_oracle_sample(h, psi, per_group=7)
+        one = cpu_oracle_sample(h, psi, per_group=1, threads=1)
         cb["one_core"] = {"value": one["value"], "unit": one["unit"], "cores": one["cores"],
                           "sample": one["sample"]}
         out["cpu_baseline"] = cb
         del psi
+    if rank == 0 and ws == 1 and not args.no_oracle_check and args.state == "c64":
+        # error of the grouped paths against the oracle on the same workload
+        out.setdefault("accuracy", {})["vs_oracle"] = oracle_accuracy(sim, h, neel, dev)
     if rank == 0:
         print(json.dumps(out))
 
