@@ -278,7 +278,10 @@ sd_status sd_prepare_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t c
  * GPU loading the library keeps until the process exits.  n qubits, state as
  * in sd_evolve; mo <= 4096 terms (more gives SD_EINVAL, with a message in
  * sd_last_error(NULL)); the observable arrays are host arrays; the value is
- * written to *out_host after the stream is synchronised.  The first call on
+ * written to *out_host after the stream is synchronised.  Each term costs
+ * one read of the state (sd_expect folds all Z-only terms into one read),
+ * so for observables with many terms on large states it is slower than
+ * sd_expect.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  All
  * calls share the array, so calls that overlap on the GPU (other streams or

@@ -139,6 +139,23 @@ def evolve(ham, psi0, dt, steps, order=1, groups=None, reps=None):
     return psi
 
 
+def evolve_inplace(ham, psi, dt, steps, order=1, groups=None):
+    """As evolve, on psi itself (a C-contiguous complex128 array) instead of
+    a copy: for states too large to hold twice in host memory."""
+    if groups is None:
+        groups = planner.greedy_partition(ham.x, ham.z)
+    if psi.dtype != np.complex128 or not psi.flags.c_contiguous:
+        raise ValueError("psi must be a C-contiguous complex128 array")
+    x = np.ascontiguousarray(ham.x, dtype=np.uint64)
+    z = np.ascontiguousarray(ham.z, dtype=np.uint64)
+    term, _, ang = sequence_arrays(groups, ham.c, dt, order)
+    lib().oracle_apply_sequence(ham.n, _p(psi.view(np.float64), ctypes.c_double),
+                                _p(x, ctypes.c_uint64), _p(z, ctypes.c_uint64),
+                                len(term), _p(term, ctypes.c_int64),
+                                _p(ang, ctypes.c_double), int(steps))
+    return psi
+
+
 def expect(psi, ox, oz, oc):
     psi = _state(psi)
     n = int(psi.shape[0]).bit_length() - 1
