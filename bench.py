@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--tile-bits", dest="tile_bits", type=int, default=0,
                     help="tile size for the batch workload (0 = default)")
     ap.add_argument("--autotune", action="store_true",
-                    help="pick the tile size by timing K = 11..13 first (sd_autotune)")
+                    help="pick the tile size (K = 11..13) and, for complex64, the register layout by "
+                         "timing them first (sd_autotune_shape)")
     ap.add_argument("--state", default="c64", choices=["c64", "c128"],
                     help="state precision of the timed leg (c64 is the benchmark line)")
     ap.add_argument("--qubits", type=int, default=30, choices=[16, 20, 24, 25, 28, 30],
@@ -318,7 +319,8 @@ def main():
     code = sd.C64 if args.state == "c64" else sd.C128
     cdt = torch.complex64 if args.state == "c64" else torch.complex128
     amp_bytes = 8 if args.state == "c64" else 16
-    tuned = sim.autotune(code, DT, steps=4, order=1, kmin=11, kmax=13) if args.autotune else None
+    # shape autotuner: tile sizes 11..13 and, for complex64, both register layouts
+    tuned = sim.autotune_shape(code, DT, steps=4, order=1, kmin=11, kmax=13) if args.autotune else None
     st64 = sim.schedule_stats(code, 1)
     launches = sim.count_passes(code, 1, args.steps)   # tile passes of the timed call
     stream = torch.cuda.current_stream()
@@ -364,7 +366,8 @@ def main():
                                 "complex128, 64-bit fixed point in the passes, Q0.64 phase angles"),
                       "l2": "state 8 GiB > 129 MB L2, no flush needed" if n == 30 else "small",
                       "parallelism": f"replicas x{ws}", "tile_bits": st64["tile_bits"],
-                      "autotune_ms_per_step": tuned[1] if tuned else None,
+                      "autotune": ({"tile_bits": tuned["tile_bits"], "layout": tuned["layout"],
+                                    "ms_per_step (K,layout)": tuned["ms_per_step"]} if tuned else None),
                       "passes_per_step": launches / args.steps,
                       "passes_per_single_step": st64["passes_per_step"]},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -90,8 +90,25 @@ typedef struct {
      * 2 = DSATUR colouring; 3 = first fit in order of decreasing |c_j| (the
      * coefficients at sd_plan time).  1 and 2 take O(m^2) time. */
     int grouping;
-    int reserved[4];
+    /* Register layout of the complex64 passes compiled at run time:
+     * -1 = plain (16 amplitudes per thread as (re, im) pairs); 1 = paired
+     * (qubit 0 kept in registers, so that a thread's amplitudes pair up along
+     * it and its one-qubit gates, rotations, shared-memory exchanges and
+     * global accesses run on packed pairs: fewer instructions, one more
+     * register round in some passes); 0 = default (plain, or what
+     * sd_autotune_shape chose).  Complex128 passes ignore it. */
+    int layout;
+    int reserved[3];
 } sd_plan_opts;
+
+/* Result of sd_autotune_shape: the shape kept, and milliseconds per step
+ * for tile sizes K = 9..13 in the plain (index 0) and paired (index 1)
+ * layouts, 0 where not run. */
+typedef struct {
+    int best_k;
+    int best_layout;          /* -1 plain, 1 paired; 0 on the on-chip path */
+    double ms[2][5];
+} sd_tune_result;
 
 /* Read-only view of a plan; pointers stay valid until the next sd_plan or
  * sd_destroy on the context. */
@@ -181,6 +198,15 @@ sd_status sd_evolve_host(sd_ctx *ctx, void *host_state, void *d_work, sd_dtype d
  * (best_k = 0).  Synchronous; SD_ENOMEM if the scratch state does not fit. */
 sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin,
                       int kmax, int *best_k, double *times_ms);
+
+/* Shape autotuner: as sd_autotune, over tile sizes K = kmin..kmax and, for
+ * complex64 states whose passes are compiled at run time, over both
+ * register layouts (plain and paired, see sd_plan_opts.layout); the
+ * fastest (K, layout) is kept for this dtype until the next sd_plan (a tile
+ * size or layout given to sd_plan overrides the tuned one).  Synchronous;
+ * scratch state and errors as for sd_autotune; *out may not be NULL. */
+sd_status sd_autotune_shape(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin,
+                            int kmax, sd_tune_result *out);
 
 /* Compiles, host only (no GPU, no CUDA driver needed: NVRTC only), the
  * kernels that sd_evolve(ctx, ., dtype, ., steps, order, .) would compile

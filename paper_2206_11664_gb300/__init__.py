@@ -128,10 +128,11 @@ class Simulator:
             pass
 
     # ------------------------------------------------------------ planning
-    def plan(self, skip_rule=-1, tile_bits=0, jit=0, grouping=0):
+    def plan(self, skip_rule=-1, tile_bits=0, jit=0, grouping=0, layout=0):
         """Host planning.  jit: 0 automatic, 1 always, -1 never; grouping:
-        0 first fit, 1 largest first, 2 DSATUR, 3 by |c| (see sd.h)."""
-        o = N.PlanOpts(skip_rule, tile_bits, jit, grouping)
+        0 first fit, 1 largest first, 2 DSATUR, 3 by |c|; layout of the
+        complex64 run-time passes: 0 default, -1 plain, 1 paired (see sd.h)."""
+        o = N.PlanOpts(skip_rule, tile_bits, jit, grouping, layout)
         self._check(self._lib.sd_plan(self._h, ctypes.byref(o)))
         return self
 
@@ -186,6 +187,57 @@ class Simulator:
         self._check(self._lib.sd_autotune(self._h, dtype, float(dt), int(steps), int(order), kmin, kmax,
                                           ctypes.byref(best), times.ctypes.data_as(N.P_dbl)))
         return best.value, {kmin + i: float(t) for i, t in enumerate(times) if t > 0}
+
+    def autotune_shape(self, dtype, dt, steps=4, order=1, kmin=None, kmax=None, cache=None):
+        """Time tile sizes kmin..kmax and, for complex64 passes compiled at
+        run time, both register layouts (sd_autotune_shape); the fastest
+        shape is kept for `dtype`.  Returns {"tile_bits", "layout",
+        "ms_per_step": {(K, layout): ms}}.  With `cache` (a JSON file path),
+        a shape stored there for this Hamiltonian, dtype, order and dt is
+        applied by re-planning with it instead of timing, and a newly timed
+        shape is stored."""
+        import hashlib
+        import json
+        import os
+        kmax = 13 if kmax is None else int(kmax)
+        kmin = max(9, kmax - 2) if kmin is None else int(kmin)
+        key = None
+        if cache is not None:
+            v = self.plan_view()
+            hsh = hashlib.sha256()
+            for name in ("group_terms", "masks", "signs", "gates"):
+                hsh.update(np.ascontiguousarray(v[name]).tobytes())
+            key = f"n{self.n}_m{self.m}_{'c128' if dtype == C128 else 'c64'}_o{int(order)}_dt{float(dt)!r}_" \
+                  f"s{int(steps)}_k{kmin}-{kmax}_{hsh.hexdigest()[:16]}"
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    known = json.load(f)
+                if key in known:
+                    got = known[key]
+                    self.plan(tile_bits=got["tile_bits"], layout=got["layout"])
+                    got = dict(got)
+                    got["cached"] = True
+                    return got
+        r = N.TuneResult()
+        self._check(self._lib.sd_autotune_shape(self._h, dtype, float(dt), int(steps), int(order), kmin, kmax,
+                                                ctypes.byref(r)))
+        ms = {}
+        for li, lay in ((0, -1), (1, 1)):
+            for k in range(kmin, kmax + 1):
+                if r.ms[li][k - 9] > 0:
+                    ms[f"{k},{lay}"] = float(r.ms[li][k - 9])
+        out = {"tile_bits": r.best_k, "layout": r.best_layout, "ms_per_step": ms, "cached": False}
+        if key is not None and r.best_k > 0:
+            known = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    known = json.load(f)
+            known[key] = {"tile_bits": r.best_k, "layout": r.best_layout, "ms_per_step": ms}
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(known, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return out
 
     def precompile(self, dtype, steps, order=1):
         """Compile (host only, NVRTC) the kernels evolve(., dt, steps, order)

@@ -22,7 +22,11 @@ STATUS_NAMES = {0: "SD_OK", 1: "SD_EINVAL", 2: "SD_ENOMEM", 3: "SD_ECUDA", 4: "S
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("skip_rule", c_int), ("tile_bits", c_int), ("jit", c_int), ("grouping", c_int),
-                ("reserved", c_int * 4)]
+                ("layout", c_int), ("reserved", c_int * 3)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best_k", c_int), ("best_layout", c_int), ("ms", (c_dbl * 5) * 2)]
 
 
 class PlanView(ctypes.Structure):
@@ -48,6 +52,7 @@ SIGNATURES = {
     "sd_get_schedule": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(ScheduleStats)]),
     "sd_prepare": (c_int, [c_vp, c_int, c_dbl, c_i64, c_int]),
     "sd_autotune": (c_int, [c_vp, c_int, c_dbl, c_i64, c_int, c_int, c_int, ctypes.POINTER(c_int), P_dbl]),
+    "sd_autotune_shape": (c_int, [c_vp, c_int, c_dbl, c_i64, c_int, c_int, c_int, ctypes.POINTER(TuneResult)]),
     "sd_evolve_host": (c_int, [c_vp, c_vp, c_vp, c_int, c_dbl, c_i64, c_int, c_vp]),
     "sd_precompile": (c_int, [c_vp, c_int, c_i64, c_int, ctypes.POINTER(c_i64)]),
     "sd_count_passes": (c_int, [c_vp, c_int, c_int, c_i64, ctypes.POINTER(c_i64)]),

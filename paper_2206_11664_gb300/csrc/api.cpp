@@ -70,6 +70,8 @@ struct sd_ctx {
     int tile_bits_opt = 0;
     int tuned_k[2] = {0, 0};   // tile size chosen by sd_autotune (complex64, complex128)
     int jit_opt = 0;
+    int layout_opt = 0;        // sd_plan_opts.layout
+    int tuned_layout = 0;      // complex64 layout chosen by sd_autotune_shape (1 paired, -1 plain)
     std::string jit_note;    // why the last program did not use run-time specialisation
     // plan view storage
     std::vector<int64_t> v_goff, v_gterms, v_gateoff;
@@ -162,8 +164,12 @@ sd_status device_tables(sd_ctx *ctx, DevTables &out) {
         return SD_OK;
     }
     const long double pi = 3.141592653589793238462643383279502884L;
-    std::vector<double2> tw(256);
+    std::vector<double2> tw(768);
     std::vector<longlong2> fxt(512);
+    for (int k = 0; k < 512; k++) {
+        const long double a = 2.0L * pi * k / 512.0L;
+        tw[256 + k] = make_double2((double)cosl(a), (double)sinl(a));
+    }
     for (int k = 0; k < 256; k++) {
         const long double a = 2.0L * pi * k / 256.0L, b = 2.0L * pi * k / 65536.0L;
         tw[k] = make_double2((double)cosl(a), (double)sinl(a));
@@ -208,11 +214,11 @@ void append_circuit(Circuit &a, const Circuit &b) {
 // Pass schedule of a canonicalised circuit on the tile path: the default
 // tile size, or smaller tiles when a pass's staged terms do not fit beside
 // the tile in shared memory.
-sd_status schedule_for(sd_ctx *ctx, const Circuit &circ, bool dbl, Schedule &S) {
+sd_status schedule_for(sd_ctx *ctx, const Circuit &circ, bool dbl, Schedule &S, bool pin0 = false) {
     int K = default_tile_bits(ctx, dbl);
     const int c = dbl ? 3 : 4;
     for (;;) {
-        std::string e = schedule_circuit(circ, ctx->n, K, c, S);
+        std::string e = schedule_circuit(circ, ctx->n, K, c, S, pin0);
         if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
         size_t need = 0;
         for (auto &p : S.passes) need = std::max(need, pass_smem_bytes(p, dbl ? 16 : 8, K));
@@ -233,6 +239,16 @@ bool jit_wanted(const sd_ctx *ctx, bool allow_jit, int64_t passes) {
     if (const char *e = getenv("SD_JIT")) mode = atoi(e) > 0 ? 1 : (e[0] == '0' ? -1 : mode);
     if (passes <= 0) return false;
     return mode > 0 || (mode == 0 && allow_jit && ctx->n >= 20 && passes <= kJitMaxPasses);
+}
+
+// With the paired layout, complex64 programs that will probably be compiled
+// at run time are scheduled with tile position 0 pinned to register slot 0,
+// which the paired pass code needs (the interpreter runs such schedules as
+// well, should the compilation not happen).
+bool pin0_wanted(const sd_ctx *ctx, bool dbl, bool allow_jit) {
+    if (dbl) return false;
+    const int layout = ctx->layout_opt != 0 ? ctx->layout_opt : ctx->tuned_layout;
+    return layout > 0 && jit_wanted(ctx, allow_jit, 1);
 }
 
 // Build and upload a program for a circuit.
@@ -272,7 +288,7 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
         return SD_OK;
     }
     Schedule S;
-    sd_status ss = schedule_for(ctx, circ, dbl, S);
+    sd_status ss = schedule_for(ctx, circ, dbl, S, pin0_wanted(ctx, dbl, allow_jit));
     if (ss != SD_OK) return ss;
     DevSchedule &D = P.sched;
     DevTables tabs;
@@ -522,7 +538,7 @@ sd_status segment_passes(sd_ctx *ctx, bool dbl, int order, int kind, int reps, i
     Circuit c = segment_circuit(ctx, order, kind, 0.01, reps);
     canonicalize_1q(c, ctx->n);
     Schedule S;
-    sd_status s = schedule_for(ctx, c, dbl, S);
+    sd_status s = schedule_for(ctx, c, dbl, S, pin0_wanted(ctx, dbl, kind == 0 || kind == 2 || kind == 4));
     if (s == SD_OK) out = (int64_t)S.passes.size();
     return s;
 }
@@ -780,12 +796,14 @@ sd_status sd_set_coeffs(sd_ctx *ctx, const double *coeffs) {
 
 sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
-    int rule = 2, tb = 0, jit = 0, grouping = 0;
+    int rule = 2, tb = 0, jit = 0, grouping = 0, layout = 0;
     if (opts) {
         rule = opts->skip_rule < 0 ? 2 : opts->skip_rule;
         tb = opts->tile_bits;
         jit = opts->jit;
         grouping = opts->grouping;
+        layout = opts->layout;
+        if (layout < -1 || layout > 1) return fail(ctx, SD_EINVAL, "layout must be -1, 0 or 1");
         if (rule > 2) return fail(ctx, SD_EINVAL, "skip_rule must be -1, 0, 1 or 2");
         if (tb != 0 && (tb < 9 || tb > 13)) return fail(ctx, SD_EINVAL, "tile_bits must be 0 or 9..13");
         if (grouping < 0 || grouping > 3) return fail(ctx, SD_EINVAL, "grouping must be 0, 1, 2 or 3");
@@ -805,6 +823,8 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     ctx->tile_bits_opt = tb;
     ctx->tuned_k[0] = ctx->tuned_k[1] = 0;
     ctx->jit_opt = jit;
+    ctx->layout_opt = layout;
+    ctx->tuned_layout = 0;
     ctx->planned = true;
     // plan view
     ctx->v_goff.assign(1, 0);
@@ -863,7 +883,7 @@ sd_status sd_get_schedule(sd_ctx *ctx, sd_dtype dtype, int order, sd_schedule_st
     Circuit c = segment_circuit(ctx, order, (order == 2 && G > 1) ? 2 : 0, 0.01);
     canonicalize_1q(c, ctx->n);
     Schedule S;   // as sd_evolve schedules it (smaller tiles if a pass's terms need the room)
-    sd_status s = schedule_for(ctx, c, dbl, S);
+    sd_status s = schedule_for(ctx, c, dbl, S, pin0_wanted(ctx, dbl, true));
     if (s != SD_OK) return s;
     out->tile_bits = S.K;
     out->passes_per_step = (int64_t)S.passes.size();
@@ -884,8 +904,14 @@ sd_status sd_prepare(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int 
     return evolve_impl(ctx, nullptr, dtype == SD_C128, dt, steps, order, nullptr, false);
 }
 
-sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin, int kmax,
-                      int *best_k, double *times_ms) {
+namespace {
+
+// Times sd_evolve(., dt, steps, order) on a scratch state for every tile size
+// K = kmin..kmax and every layout of `layouts` (complex64 only: -1 plain,
+// 1 paired), after one untimed call that builds and compiles the programs;
+// keeps the fastest pair for the dtype.  ms[l][K - 9] receives ms per step.
+sd_status autotune_impl(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin, int kmax,
+                        const std::vector<int> &layouts, int *best_k, int *best_layout, double ms[2][5]) {
     if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
     if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");
     if (dtype != SD_C64 && dtype != SD_C128) return fail(ctx, SD_EINVAL, "dtype must be SD_C64 or SD_C128");
@@ -895,9 +921,10 @@ sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int
         return fail(ctx, SD_EINVAL, "tile sizes must satisfy 9 <= kmin <= kmax <= 13");
     const bool dbl = dtype == SD_C128;
     const int d = dbl ? 1 : 0;
-    if (times_ms)
-        for (int k = kmin; k <= kmax; k++) times_ms[k - kmin] = 0.0;
-    if (best_k) *best_k = 0;
+    for (int l = 0; l < 2; l++)
+        for (int k = 0; k < 5; k++) ms[l][k] = 0.0;
+    *best_k = 0;
+    *best_layout = 0;
     sd_status s = ensure_device(ctx);
     if (s != SD_OK) return s;
     if (use_onchip(ctx, dbl)) return SD_OK;   // nothing to tune: one launch runs every step
@@ -914,8 +941,8 @@ sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int
     }
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const int saved = ctx->tuned_k[d];
-    int best = 0;
+    const int saved = ctx->tuned_k[d], saved_layout = ctx->tuned_layout;
+    int best = 0, best_l = 0;
     double best_ms = 0.0;
     s = SD_OK;
     cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -923,44 +950,82 @@ sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(scratch, 0, bytes, st);
     if (ce != cudaSuccess) s = fail(ctx, SD_ECUDA, std::string("autotune: ") + cudaGetErrorString(ce));
-    for (int K = kmin; K <= kmax && s == SD_OK; K++) {
-        if (K > ctx->n) break;
-        ctx->tuned_k[d] = K;
-        drop_programs();
-        // warm-up call of the timed shape (builds and compiles its programs)
-        sd_status r = evolve_impl(ctx, scratch, dbl, dt, steps, order, st);
-        if (r == SD_OK && cudaStreamSynchronize(st) != cudaSuccess) r = SD_ECUDA;
-        if (r != SD_OK) {
-            // a tile size the scheduler or the device cannot run is skipped
-            cudaGetLastError();
-            continue;
-        }
-        cudaEventRecord(e0, st);
-        r = evolve_impl(ctx, scratch, dbl, dt, steps, order, st);
-        cudaEventRecord(e1, st);
-        if (r != SD_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-            s = fail(ctx, SD_ECUDA, "autotune: timed run failed");
-            break;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double per = (double)ms / (double)steps;
-        if (times_ms) times_ms[K - kmin] = per;
-        if (best == 0 || per < best_ms) {
-            best = K;
-            best_ms = per;
+    for (int L : layouts) {
+        if (!dbl) ctx->tuned_layout = L;
+        for (int K = kmin; K <= kmax && s == SD_OK; K++) {
+            if (K > ctx->n) break;
+            ctx->tuned_k[d] = K;
+            drop_programs();
+            // warm-up call of the timed shape (builds and compiles its programs)
+            sd_status r = evolve_impl(ctx, scratch, dbl, dt, steps, order, st);
+            if (r == SD_OK && cudaStreamSynchronize(st) != cudaSuccess) r = SD_ECUDA;
+            if (r != SD_OK) {
+                // a tile size the scheduler or the device cannot run is skipped
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, st);
+            r = evolve_impl(ctx, scratch, dbl, dt, steps, order, st);
+            cudaEventRecord(e1, st);
+            if (r != SD_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                s = fail(ctx, SD_ECUDA, "autotune: timed run failed");
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            const double per = (double)t / (double)steps;
+            ms[L > 0 ? 1 : 0][K - 9] = per;
+            if (best == 0 || per < best_ms) {
+                best = K;
+                best_l = L;
+                best_ms = per;
+            }
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);
     cudaFree(scratch);
-    ctx->tuned_k[d] = s == SD_OK && best > 0 ? best : saved;
+    const bool ok = s == SD_OK && best > 0;
+    ctx->tuned_k[d] = ok ? best : saved;
+    if (!dbl) ctx->tuned_layout = ok ? best_l : saved_layout;
     drop_programs();
     if (s != SD_OK) return s;
     if (best == 0) return fail(ctx, SD_EINVAL, "no tile size in the range could be scheduled");
-    if (best_k) *best_k = best;
+    *best_k = best;
+    *best_layout = best_l;
     return SD_OK;
+}
+
+}  // namespace
+
+sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin, int kmax,
+                      int *best_k, double *times_ms) {
+    int bk = 0, bl = 0;
+    double ms[2][5];
+    // the layout in force (sd_plan's, else the tuned one, else plain) is kept
+    int L = -1;
+    if (ctx) L = ctx->layout_opt != 0 ? ctx->layout_opt : (ctx->tuned_layout != 0 ? ctx->tuned_layout : -1);
+    if (times_ms && kmin <= kmax)
+        for (int k = kmin; k <= kmax; k++) times_ms[k - kmin] = 0.0;
+    if (best_k) *best_k = 0;
+    sd_status s = autotune_impl(ctx, dtype, dt, steps, order, kmin, kmax, {L}, &bk, &bl, ms);
+    if (s != SD_OK) return s;
+    if (times_ms)
+        for (int k = kmin; k <= kmax; k++) times_ms[k - kmin] = ms[L > 0 ? 1 : 0][k - 9];
+    if (best_k) *best_k = bk;
+    return SD_OK;
+}
+
+sd_status sd_autotune_shape(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin,
+                            int kmax, sd_tune_result *out) {
+    if (!out) return fail(ctx, SD_EINVAL, "null result pointer");
+    memset(out, 0, sizeof(*out));
+    std::vector<int> layouts{-1};
+    // the paired layout exists for complex64 passes compiled at run time
+    if (ctx && dtype == SD_C64 && ctx->layout_opt == 0 && jit_wanted(ctx, true, 1)) layouts.push_back(1);
+    else if (ctx && dtype == SD_C64 && ctx->layout_opt != 0) layouts.assign(1, ctx->layout_opt);
+    return autotune_impl(ctx, dtype, dt, steps, order, kmin, kmax, layouts, &out->best_k, &out->best_layout, out->ms);
 }
 
 sd_status sd_evolve_host(sd_ctx *ctx, void *host_state, void *d_work, sd_dtype dtype, double dt,
@@ -1013,8 +1078,8 @@ sd_status sd_precompile(sd_ctx *ctx, sd_dtype dtype, int64_t steps, int order, i
         Circuit c = segment_circuit(ctx, order, sg.first, 0.01, sg.second);
         canonicalize_1q(c, ctx->n);
         Schedule S;
-        if ((s = schedule_for(ctx, c, dbl, S)) != SD_OK) return s;
         const bool allow = sg.first == 0 || sg.first == 2 || sg.first == 4;
+        if ((s = schedule_for(ctx, c, dbl, S, pin0_wanted(ctx, dbl, allow))) != SD_OK) return s;
         if (!jit_wanted(ctx, allow, (int64_t)S.passes.size())) continue;
         int done = 0;
         const std::string e = jit_precompile(S, ctx->n, dbl, &done);

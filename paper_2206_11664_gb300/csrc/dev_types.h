@@ -166,7 +166,8 @@ struct KParams {
     const uint64_t *cst_mo;
     const int64_t *cst_q;
     int c;
-    // per-device constant tables: e^{2 pi i k/256} (FP64), and in Q1.62
+    // per-device constant tables: e^{2 pi i k/256} (FP64, entries 0..255)
+    // and e^{2 pi i k/512} (FP64, entries 256..767); in Q1.62
     // e^{2 pi i k/256} (entries 0..255) and e^{2 pi i k/65536} (256..511)
     const double2 *tw;
     const longlong2 *fxt;

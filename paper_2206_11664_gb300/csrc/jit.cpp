@@ -202,12 +202,126 @@ bool diag_class_used(const DevDiag &d, int u) {
     return d.off[u + 1] > d.off[u] || d.zs[u] >= 0 || (u == 0 && d.cst >= 0);
 }
 
+// Staging of a round's group exponentials for the tile (slot sums, tile
+// constants, class totals), with the barriers around it.  Complex64 passes
+// bias the class totals by 2^31 (rounding to Q0.32 turns), complex128 passes
+// keep Q0.64.
+void emit_round_staging(std::ostringstream &o, const Schedule &S, const DevPass &P, const DevRound &R, int NT,
+                        bool dbl_state) {
+    // Straight-line code only for rounds of modest size: longer code
+    // compiles slowly and gains nothing once the work is spread out.
+    int round_terms = 0;
+    for (int j = 0; j < R.slot_count; j++) round_terms += S.slots[R.slot_begin + j].tn;
+    const bool inline_stage = round_terms <= kInlineTerms && R.slot_count <= kInlineSlots;
+    if (P.term_cache && !inline_stage) {
+        o << "      stage_slots(xo, kp.slots, " << R.slot_begin << ", " << R.slot_count
+          << ", TCM, TCQ, " << P.term_begin << ", ST, tid, NT);\n";
+    } else if (P.term_cache) {
+        // one thread per slot, spread over the warps; masks inline, angles from the cache
+        for (int j = 0; j < R.slot_count; j++) {
+            const DevSlot &sl = S.slots[R.slot_begin + j];
+            const int thr = ((j * 32) % NT + (j * 32) / NT) % NT;
+            o << "      if (tid == " << thr << ") { uint64_t acc = 0ull;\n";
+            for (int t = sl.tb; t < sl.tb + sl.tn; t++) {
+                const int i = t - P.term_begin;
+                o << "        { const uint64_t v = (uint64_t)TCQ[" << i << "]; acc += (__popcll(xo & "
+                  << hex64(S.term_mo[t]) << ") & 1) ? 0ull - v : v; }\n";
+            }
+            o << "        ST[" << j << "].q = acc; ST[" << j << "].ml = " << hex32(sl.ml) << "; }\n";
+        }
+    } else {
+        o << "      stage_slots(xo, kp.slots, " << R.slot_begin << ", " << R.slot_count
+          << ", kp.term_mo, kp.term_q, 0, ST, tid, NT);\n";
+    }
+    for (int cc = 0; cc < 4; cc++)
+        if (R.cst_count[cc] > 0)
+            o << "      if (warp == " << (cc % (NT / 32)) << ") { const uint64_t v = warp_const_sum(xo, kp.cst_mo, kp.cst_q, "
+              << R.cst_begin[cc] << ", " << R.cst_count[cc] << ", lane); if (lane == 0) CST[" << cc << "] = v; }\n";
+    o << "      __syncthreads();\n";
+    // class totals, one thread each, spread over the warps
+    if (!inline_stage)
+        o << "      stage_totals(kp, " << R.diag_begin << ", " << R.n_diag << ", ST, CST, "
+          << hex64(dbl_state ? 0 : (1ull << 31)) << ", TQ, tid, NT);\n";
+    for (int k = 0; k < R.n_diag && inline_stage; k++) {
+        const DevDiag &d = S.diags[R.diag_begin + k];
+        for (int u = 0; u < 16; u++) {
+            if (!diag_class_used(d, u)) continue;
+            const int i = d.tot + u;
+            const int thr = ((i * 32) % NT + (i * 32) / NT) % NT;
+            o << "      if (tid == " << thr << ") TQ[" << i << "] = " << hex64(dbl_state ? 0 : (1ull << 31));
+            if (d.zs[u] >= 0) o << " + ST[" << d.zs[u] << "].q";
+            for (int j = d.off[u]; j < d.off[u + 1]; j++) o << " + ST[" << j << "].q";
+            if (u == 0 && d.cst >= 0) o << " + CST[" << d.cst << "]";
+            o << ";\n";
+        }
+    }
+    o << "      __syncthreads();\n";
+}
+
+// Class sums G[u] of a group exponential for the thread (fixed positions lf):
+// the class total less twice its slots of odd parity with lf.
+void emit_class_sums(std::ostringstream &o, const Schedule &S, const DevRound &R, const DevDiag &d) {
+    const bool unrolled = d.off[16] <= kInlineSlots;
+    for (int u = 0; u < 16; u++) {
+        if (!diag_class_used(d, u)) {
+            o << "        G[" << u << "] = 0ull;\n";
+            continue;
+        }
+        const int b = d.off[u], e = d.off[u + 1];
+        o << "        { uint64_t o0 = 0ull, o1 = 0ull;\n";
+        if (unrolled) {
+            for (int j = b; j < e; j++) {
+                const uint32_t ml = S.slots[R.slot_begin + j].ml;
+                const char *acc = ((j - b) & 1) ? "o1" : "o0";
+                if ((ml & (ml - 1)) == 0)
+                    o << "          if (lf & " << hex32(ml) << ") " << acc << " += ST[" << j << "].q;\n";
+                else
+                    o << "          if (__popc(lf & " << hex32(ml) << ") & 1) " << acc << " += ST[" << j
+                      << "].q;\n";
+            }
+        } else if (e > b) {
+            o << "          #pragma unroll 4\n"
+              << "          for (int j = " << b << "; j < " << e << "; j++) {\n"
+              << "            const StagedTerm t0 = ST[j];\n"
+              << "            if (__popc(lf & t0.ml) & 1) o0 += t0.q;\n"
+              << "          }\n";
+        }
+        o << "          G[" << u << "] = TQ[" << d.tot + u << "] - 2ull * (o0 + o1); }\n";
+    }
+}
+
+// The tile bookkeeping every pass kernel opens with: the thread's share of
+// the prefetch copy, the tile count, the outer-bit deposit of a tile index
+// and the cp.async prefetch of a tile into Pf (natural tile order, E
+// amplitudes per 16-byte copy).
+void emit_io_prologue(std::ostringstream &o, const DevPass &P, int K, int NT, int E, int n) {
+    auto gbit = [&](int p) -> uint64_t { return (uint64_t)1 << P.tile_bits[p]; };
+    const int NCOPY = (1 << K) / E / NT;
+    // copy l = (tid + k NT) E: bit j of l is bit (j - log2 E) of tid for the low K-4 such bits
+    const int le = E == 2 ? 1 : 0;
+    o << "  const uint64_t sp_tid = 0ull";
+    for (int j = le; j < K; j++)
+        if (j - le < K - 4) o << " | ((uint64_t)((tid >> " << (j - le) << ") & 1) << " << (int)P.tile_bits[j] << ")";
+    o << ";\n  const long long ntiles = " << (1LL << (n - K)) << "ll;\n"
+      << "  auto deposit = [&](long long t) -> uint64_t {\n"
+      << "    return OUTT[0][t & 255] | OUTT[1][(t >> 8) & 255] | OUTT[2][(t >> 16) & 255] | OUTT[3][(t >> 24) & 255];\n"
+      << "  };\n"
+      << "  auto prefetch = [&](long long t) {\n    const uint64_t xo = deposit(t) | sp_tid;\n";
+    for (int k = 0; k < NCOPY; k++) {
+        const uint64_t lk = (uint64_t)k * NT * E;
+        uint64_t off = 0;
+        for (int j = 0; j < K; j++)
+            if ((lk >> j) & 1) off |= gbit(j);
+        o << "    cp_async16(Pf + (tid * E + " << lk << "), psi + (xo | " << hex64(off) << "));\n";
+    }
+    o << "    cp_async_commit();\n  };\n";
+}
+
 std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     const DevPass &P = S.passes[pi];
     const int K = S.K, c = S.c;
     const int NT = 1 << (K - 4);
     const int E = dbl_state ? 1 : 2;
-    const int NCOPY = (1 << K) / E / NT;
     auto gbit = [&](int p) -> uint64_t { return (uint64_t)1 << P.tile_bits[p]; };
     auto swc = [&](int p) -> uint64_t { return swizzle_col(p, c); };
     auto lcol = [&](int p) -> uint64_t { return (uint64_t)1 << p; };
@@ -291,24 +405,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         o << ";\n";
     }
     o << "  }\n  __syncthreads();\n";
-    // copy l = (tid + k NT) E: bit j of l is bit (j - log2 E) of tid for the low K-4 such bits
-    const int le = E == 2 ? 1 : 0;
-    o << "  const uint64_t sp_tid = 0ull";
-    for (int j = le; j < K; j++)
-        if (j - le < K - 4) o << " | ((uint64_t)((tid >> " << (j - le) << ") & 1) << " << (int)P.tile_bits[j] << ")";
-    o << ";\n  const long long ntiles = " << (1LL << (n - K)) << "ll;\n"
-      << "  auto deposit = [&](long long t) -> uint64_t {\n"
-      << "    return OUTT[0][t & 255] | OUTT[1][(t >> 8) & 255] | OUTT[2][(t >> 16) & 255] | OUTT[3][(t >> 24) & 255];\n"
-      << "  };\n"
-      << "  auto prefetch = [&](long long t) {\n    const uint64_t xo = deposit(t) | sp_tid;\n";
-    for (int k = 0; k < NCOPY; k++) {
-        const uint64_t lk = (uint64_t)k * NT * E;
-        uint64_t off = 0;
-        for (int j = 0; j < K; j++)
-            if ((lk >> j) & 1) off |= gbit(j);
-        o << "    cp_async16(Pf + (tid * E + " << lk << "), psi + (xo | " << hex64(off) << "));\n";
-    }
-    o << "    cp_async_commit();\n  };\n";
+    emit_io_prologue(o, P, K, NT, E, n);
     // swizzle of an arbitrary tile index (perm rounds)
     o << "  auto swz = [](uint32_t v) -> uint32_t {\n    return 0u";
     for (int p = 0; p < K; p++) o << " ^ (((v >> " << p << ") & 1u) * " << hex32((uint32_t)swc(p)) << ")";
@@ -323,56 +420,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         o << "    { // round " << r << "\n";
         if (r == 0) o << "      cp_async_wait_all();\n";
         o << "      __syncthreads();\n";
-        if (R.n_diag > 0) {
-            // Straight-line code only for rounds of modest size: longer code
-            // compiles slowly and gains nothing once the work is spread out.
-            int round_terms = 0;
-            for (int j = 0; j < R.slot_count; j++) round_terms += S.slots[R.slot_begin + j].tn;
-            const bool inline_stage = round_terms <= kInlineTerms && R.slot_count <= kInlineSlots;
-            if (P.term_cache && !inline_stage) {
-                o << "      stage_slots(xo, kp.slots, " << R.slot_begin << ", " << R.slot_count
-                  << ", TCM, TCQ, " << P.term_begin << ", ST, tid, NT);\n";
-            } else if (P.term_cache) {
-                // one thread per slot, spread over the warps; masks inline, angles from the cache
-                for (int j = 0; j < R.slot_count; j++) {
-                    const DevSlot &sl = S.slots[R.slot_begin + j];
-                    const int thr = ((j * 32) % NT + (j * 32) / NT) % NT;
-                    o << "      if (tid == " << thr << ") { uint64_t acc = 0ull;\n";
-                    for (int t = sl.tb; t < sl.tb + sl.tn; t++) {
-                        const int i = t - P.term_begin;
-                        o << "        { const uint64_t v = (uint64_t)TCQ[" << i << "]; acc += (__popcll(xo & "
-                          << hex64(S.term_mo[t]) << ") & 1) ? 0ull - v : v; }\n";
-                    }
-                    o << "        ST[" << j << "].q = acc; ST[" << j << "].ml = " << hex32(sl.ml) << "; }\n";
-                }
-            } else {
-                o << "      stage_slots(xo, kp.slots, " << R.slot_begin << ", " << R.slot_count
-                  << ", kp.term_mo, kp.term_q, 0, ST, tid, NT);\n";
-            }
-            for (int cc = 0; cc < 4; cc++)
-                if (R.cst_count[cc] > 0)
-                    o << "      if (warp == " << (cc % (NT / 32)) << ") { const uint64_t v = warp_const_sum(xo, kp.cst_mo, kp.cst_q, "
-                      << R.cst_begin[cc] << ", " << R.cst_count[cc] << ", lane); if (lane == 0) CST[" << cc << "] = v; }\n";
-            o << "      __syncthreads();\n";
-            // class totals, one thread each, spread over the warps
-            if (!inline_stage)
-                o << "      stage_totals(kp, " << R.diag_begin << ", " << R.n_diag << ", ST, CST, "
-                  << hex64(dbl_state ? 0 : (1ull << 31)) << ", TQ, tid, NT);\n";
-            for (int k = 0; k < R.n_diag && inline_stage; k++) {
-                const DevDiag &d = S.diags[R.diag_begin + k];
-                for (int u = 0; u < 16; u++) {
-                    if (!diag_class_used(d, u)) continue;
-                    const int i = d.tot + u;
-                    const int thr = ((i * 32) % NT + (i * 32) / NT) % NT;
-                    o << "      if (tid == " << thr << ") TQ[" << i << "] = " << hex64(dbl_state ? 0 : (1ull << 31));
-                    if (d.zs[u] >= 0) o << " + ST[" << d.zs[u] << "].q";
-                    for (int j = d.off[u]; j < d.off[u + 1]; j++) o << " + ST[" << j << "].q";
-                    if (u == 0 && d.cst >= 0) o << " + CST[" << d.cst << "]";
-                    o << ";\n";
-                }
-            }
-            o << "      __syncthreads();\n";
-        }
+        if (R.n_diag > 0) emit_round_staging(o, S, P, R, NT, dbl_state);
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t sw = " << thread_expr(R, K, swc, false) << ";\n"
           << "      (void)lf; (void)sw;\n";
@@ -443,33 +491,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                 const DevDiag &d = S.diags[op.arg];
                 const double sc = (op.pad && !table_scaled) ? P.scale : 1.0;
                 o << "      { uint64_t G[16];\n";
-                const bool unrolled = d.off[16] <= kInlineSlots;
-                for (int u = 0; u < 16; u++) {
-                    if (!diag_class_used(d, u)) {
-                        o << "        G[" << u << "] = 0ull;\n";
-                        continue;
-                    }
-                    const int b = d.off[u], e = d.off[u + 1];
-                    o << "        { uint64_t o0 = 0ull, o1 = 0ull;\n";
-                    if (unrolled) {
-                        for (int j = b; j < e; j++) {
-                            const uint32_t ml = S.slots[R.slot_begin + j].ml;
-                            const char *acc = ((j - b) & 1) ? "o1" : "o0";
-                            if ((ml & (ml - 1)) == 0)
-                                o << "          if (lf & " << hex32(ml) << ") " << acc << " += ST[" << j << "].q;\n";
-                            else
-                                o << "          if (__popc(lf & " << hex32(ml) << ") & 1) " << acc << " += ST[" << j
-                                  << "].q;\n";
-                        }
-                    } else if (e > b) {
-                        o << "          #pragma unroll 4\n"
-                          << "          for (int j = " << b << "; j < " << e << "; j++) {\n"
-                          << "            const StagedTerm t0 = ST[j];\n"
-                          << "            if (__popc(lf & t0.ml) & 1) o0 += t0.q;\n"
-                          << "          }\n";
-                    }
-                    o << "          G[" << u << "] = TQ[" << d.tot + u << "] - 2ull * (o0 + o1); }\n";
-                }
+                emit_class_sums(o, S, R, d);
                 if (fx)
                     o << "        wht16(G);\n"
                       << "        #pragma unroll\n"
@@ -548,6 +570,252 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     return o.str();
 }
 
+// Whether pass pi runs the paired complex64 code (gen_pass_packed): its
+// schedule keeps tile position 0 in register slot 0, and no round of the
+// pass applies a tile permutation or a quarter-turn layer.
+bool packed_pass(const Schedule &S, int pi) {
+    if (!S.pin0) return false;
+    const DevPass &P = S.passes[pi];
+    for (int r = 0; r < P.n_rounds; r++) {
+        const DevRound &R = S.rounds[P.round_begin + r];
+        if (R.reg_pos[0] != 0 || R.perm >= 0) return false;
+        for (int oi = R.op_begin; oi < R.op_end; oi++)
+            if (S.ops[oi].kind == D_PHASE) return false;
+    }
+    return true;
+}
+
+// (x, y) <- i^k (x, y) as text: the component expressions of i^k times the
+// amplitude with components ax, ay.
+void ipow_text(int k, const std::string &ax, const std::string &ay, std::string &x, std::string &y) {
+    switch (k & 3) {
+    case 0: x = ax; y = ay; break;
+    case 1: x = "-(" + ay + ")"; y = ax; break;
+    case 2: x = "-(" + ax + ")"; y = "-(" + ay + ")"; break;
+    default: x = ay; y = "-(" + ax + ")"; break;
+    }
+}
+
+// Generated complex64 pass in the paired layout.  A thread's 16 amplitudes
+// form 8 pairs that differ only in tile position 0 (register slot 0); pair k
+// holds register slots 1..3 = the bits of k as two float2 values, R[k] =
+// (re, re) and I[k] = (im, im) of its two amplitudes.  A one-qubit Clifford
+// on slots 1..3 then treats both amplitudes of a pair with one packed f32x2
+// instruction per component; the exchange between rounds moves 16-byte
+// pairs (8 per 128-byte row, paired swizzle); the rotation of a group
+// exponential and the global loads and stores work on pairs.  Pair k is held
+// as i^-kph[k] times its value (kph fixed at generation time, as in the
+// fixed-point passes), so that the quarter-turn phases of S^b H S^a only
+// choose adds or subtracts; they are applied before each write.
+std::string gen_pass_packed(const Schedule &S, int pi, int n) {
+    const DevPass &P = S.passes[pi];
+    const int K = S.K;
+    const int NT = 1 << (K - 4);
+    const int E = 2;
+    auto gbit = [&](int p) -> uint64_t { return (uint64_t)1 << P.tile_bits[p]; };
+    auto lcol = [&](int p) -> uint64_t { return (uint64_t)1 << p; };
+    auto ucol = [&](int p) -> uint64_t { return p == 0 ? 0 : (uint64_t)pair_swizzle_col(p); };
+    const double pass_scale = P.scale_in_diag ? 1.0 : P.scale;
+    int n_diag = 0;
+    for (int r = 0; r < P.n_rounds; r++) {
+        const DevRound &R = S.rounds[P.round_begin + r];
+        for (int oi = R.op_begin; oi < R.op_end; oi++) n_diag += S.ops[oi].kind == D_DIAG;
+    }
+    const bool table_scaled = P.scale_in_diag && n_diag == 1;
+    const double table_scale = table_scaled ? P.scale : 1.0;
+    std::ostringstream o;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << kernel_name(pi, false)
+      << "(A *__restrict__ psi, sd::KParams kp) {\n"
+      << "  using namespace sd;\n"
+      << "  constexpr int K = " << K << ", NT = " << NT << ", E = " << E << ";\n"
+      << "  extern __shared__ __align__(16) unsigned char smraw[];\n"
+      << "  float4 *X4 = reinterpret_cast<float4 *>(smraw);\n"
+      << "  A *Pf = reinterpret_cast<A *>(smraw) + (1 << K);\n"
+      << "  const float4 *Pf4 = reinterpret_cast<const float4 *>(Pf);\n"
+      << "  StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf + (1 << K));\n"
+      << "  uint64_t *TQ = reinterpret_cast<uint64_t *>(ST + " << (P.max_stage > 0 ? P.max_stage : 1) << ");\n"
+      << "  (void)ST; (void)TQ;\n";
+    if (P.term_cache)
+        o << "  uint64_t *TCM = TQ + " << P.max_tot << ";\n"
+          << "  int64_t *TCQ = reinterpret_cast<int64_t *>(TCM + " << P.term_count << ");\n"
+          << "  cache_terms(kp, " << P.term_begin << ", " << P.term_count << ", TCM, TCQ, threadIdx.x, NT);\n";
+    o << "  __shared__ float TC[512], TS[512];\n"
+      << "  __shared__ uint64_t OUTT[4][256];\n"
+      << "  __shared__ uint64_t CST[4];\n"
+      << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n"
+      << "  (void)lane; (void)warp;\n"
+      << "  for (int i = tid; i < 512; i += NT) {\n"
+      << "    const double2 e = kp.tw[256 + i];\n"
+      << "    TC[i] = (float)(e.x * " << dbl(table_scale) << ");\n"
+      << "    TS[i] = (float)(e.y * " << dbl(table_scale) << ");\n"
+      << "    if (i < 256) {\n";
+    for (int byte = 0; byte < 4; byte++) {
+        o << "      OUTT[" << byte << "][i] = 0ull";
+        for (int b = 0; b < 8; b++) {
+            const int k = byte * 8 + b;
+            if (k < P.n_outer) o << " | ((uint64_t)((i >> " << b << ") & 1) << " << (int)P.outer_bits[k] << ")";
+        }
+        o << ";\n";
+    }
+    o << "    }\n  }\n  __syncthreads();\n";
+    emit_io_prologue(o, P, K, NT, E, n);
+    o << "  const float2 M1 = make_float2(-1.f, -1.f);\n  (void)M1;\n"
+      << "  long long tile = blockIdx.x;\n  if (tile < ntiles) prefetch(tile);\n"
+      << "  for (; tile < ntiles; tile += gridDim.x) {\n"
+      << "    const uint64_t xo = deposit(tile);\n"
+      << "    float2 R[8], I[8];\n";
+    // register slot i (1..3) <-> bit i-1 of the pair index k
+    auto slot_sum = [&](const DevRound &R, int k, const std::function<uint64_t(int)> &col) {
+        uint64_t v = 0;
+        for (int i = 1; i < 4; i++)
+            if ((k >> (i - 1)) & 1) v ^= col(R.reg_pos[i]);
+        return v;
+    };
+    for (int r = 0; r < P.n_rounds; r++) {
+        const DevRound &R = S.rounds[P.round_begin + r];
+        o << "    { // round " << r << "\n";
+        if (r == 0) o << "      cp_async_wait_all();\n";
+        o << "      __syncthreads();\n";
+        if (R.n_diag > 0) emit_round_staging(o, S, P, R, NT, false);
+        o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
+          << "      const uint32_t swu = " << thread_expr(R, K, ucol, false) << ";\n"
+          << "      (void)lf; (void)swu;\n";
+        if (r == 0) {
+            for (int k = 0; k < 8; k++)
+                o << "      { const float4 v = Pf4[(lf | " << hex32((uint32_t)slot_sum(R, k, lcol))
+                  << ") >> 1]; R[" << k << "] = make_float2(v.x, v.z); I[" << k << "] = make_float2(v.y, v.w); }\n";
+            o << "      __syncthreads();\n"
+              << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);\n";
+        } else {
+            for (int k = 0; k < 8; k++)
+                o << "      { const float4 v = X4[swu ^ " << hex32((uint32_t)slot_sum(R, k, ucol)) << "]; R[" << k
+                  << "] = make_float2(v.x, v.y); I[" << k << "] = make_float2(v.z, v.w); }\n";
+        }
+        if (R.flags & 2) o << "      const uint64_t xf = xo | " << thread_expr(R, K, gbit, true) << ";\n";
+        int kph[8] = {0};
+        for (int oi = R.op_begin; oi < R.op_end; oi++) {
+            const DevOp &op = S.ops[oi];
+            if ((op.kind == D_HAD || op.kind == D_MONO) && op.slot == 0) {
+                // within each pair (one frame for both amplitudes): scalar code
+                const int PA = c1_a(op.arg);
+                for (int k = 0; k < 8; k++) {
+                    const std::string ks = std::to_string(k);
+                    std::string wx, wy;
+                    ipow_text(PA, "R[" + ks + "].y", "I[" + ks + "].y", wx, wy);
+                    if (op.kind == D_HAD) {
+                        std::string tx, ty;
+                        ipow_text(c1_b(op.arg), "dx", "dy", tx, ty);
+                        o << "      { const float wx = " << wx << ", wy = " << wy << ";\n"
+                          << "        const float sx = R[" << k << "].x + wx, sy = I[" << k << "].x + wy;\n"
+                          << "        const float dx = fmaf(-2.f, wx, sx), dy = fmaf(-2.f, wy, sy);\n"
+                          << "        R[" << k << "].x = sx; I[" << k << "].x = sy; R[" << k << "].y = " << tx
+                          << "; I[" << k << "].y = " << ty << "; }\n";
+                    } else if (c1_x(op.arg)) {
+                        o << "      { const float wx = " << wx << ", wy = " << wy << ";\n"
+                          << "        R[" << k << "].y = R[" << k << "].x; I[" << k << "].y = I[" << k << "].x; R["
+                          << k << "].x = wx; I[" << k << "].x = wy; }\n";
+                    } else {
+                        o << "      { const float wx = " << wx << ", wy = " << wy << "; R[" << k << "].y = wx; I[" << k
+                          << "].y = wy; }\n";
+                    }
+                }
+            } else if (op.kind == D_HAD) {
+                const int bit = 1 << (op.slot - 1);
+                for (int k = 0; k < 8; k++) {
+                    if (k & bit) continue;
+                    const int t = k | bit;
+                    const int m = (c1_a(op.arg) + kph[t] - kph[k]) & 3;
+                    // w = i^m v in pair k's frame: component source and sign
+                    const std::string vR = "R[" + std::to_string(t) + "]", vI = "I[" + std::to_string(t) + "]";
+                    std::string srcR, srcI;
+                    int sgR, sgI;
+                    switch (m) {
+                    case 0: srcR = vR; sgR = 1; srcI = vI; sgI = 1; break;
+                    case 1: srcR = vI; sgR = -1; srcI = vR; sgI = 1; break;
+                    case 2: srcR = vR; sgR = -1; srcI = vI; sgI = -1; break;
+                    default: srcR = vI; sgR = 1; srcI = vR; sgI = -1; break;
+                    }
+                    auto add = [&](const std::string &u, const std::string &src, int sg) {
+                        return sg > 0 ? "__fadd2_rn(" + u + ", " + src + ")" : "__ffma2_rn(" + src + ", M1, " + u + ")";
+                    };
+                    auto dd = [&](const std::string &src, int sg, const std::string &su) {
+                        return "__ffma2_rn(" + src + ", make_float2(" + (sg > 0 ? "-2.f, -2.f" : "2.f, 2.f") + "), " + su +
+                               ")";
+                    };
+                    const std::string uR = "R[" + std::to_string(k) + "]", uI = "I[" + std::to_string(k) + "]";
+                    o << "      { const float2 sR = " << add(uR, srcR, sgR) << ", sI = " << add(uI, srcI, sgI) << ";\n"
+                      << "        const float2 dR = " << dd(srcR, sgR, "sR") << ", dI = " << dd(srcI, sgI, "sI") << ";\n"
+                      << "        " << uR << " = sR; " << uI << " = sI; " << vR << " = dR; " << vI << " = dI; }\n";
+                    kph[t] = (c1_b(op.arg) + kph[k]) & 3;
+                }
+            } else if (op.kind == D_MONO) {
+                const int bit = 1 << (op.slot - 1);
+                for (int k = 0; k < 8; k++) {
+                    if (k & bit) continue;
+                    const int t = k | bit;
+                    kph[t] = (kph[t] + c1_a(op.arg)) & 3;
+                    if (c1_x(op.arg)) {
+                        o << "      { const float2 tR = R[" << k << "], tI = I[" << k << "]; R[" << k << "] = R[" << t
+                          << "]; I[" << k << "] = I[" << t << "]; R[" << t << "] = tR; I[" << t << "] = tI; }\n";
+                        std::swap(kph[k], kph[t]);
+                    }
+                }
+            } else {   // D_DIAG
+                const DevDiag &d = S.diags[op.arg];
+                const double sc = (op.pad && !table_scaled) ? P.scale : 1.0;
+                o << "      { uint64_t G[16];\n";
+                emit_class_sums(o, S, R, d);
+                o << "        uint32_t g[16];\n"
+                  << "        #pragma unroll\n"
+                  << "        for (int s = 0; s < 16; s++) g[s] = (uint32_t)(G[s] >> 32);\n"
+                  << "        wht16(g);\n";
+                for (int k = 0; k < 8; k++)
+                    o << "        rotate_pair32(R[" << k << "], I[" << k << "], g[" << 2 * k << "], g[" << 2 * k + 1
+                      << "], TC, TS, (float)" << dbl(sc) << ");\n";
+                o << "      }\n";
+            }
+        }
+        // back to the amplitudes' own frame (and the pass scale before a store)
+        const double ws = (R.flags & 2) ? pass_scale : 1.0;
+        for (int k = 0; k < 8; k++) {
+            const std::string ks = std::to_string(k);
+            const std::string f = ws == 1.0 ? "M1" : "make_float2((float)" + dbl(-ws) + ", (float)" + dbl(-ws) + ")";
+            const std::string fp = "make_float2((float)" + dbl(ws) + ", (float)" + dbl(ws) + ")";
+            switch (kph[k]) {
+            case 0:
+                if (ws != 1.0)
+                    o << "      R[" << ks << "] = __fmul2_rn(R[" << ks << "], " << fp << "); I[" << ks
+                      << "] = __fmul2_rn(I[" << ks << "], " << fp << ");\n";
+                break;
+            case 1:   // i (R + iI) = -I + iR
+                o << "      { const float2 t = R[" << ks << "]; R[" << ks << "] = __fmul2_rn(I[" << ks << "], " << f
+                  << "); I[" << ks << "] = " << (ws == 1.0 ? "t" : "__fmul2_rn(t, " + fp + ")") << "; }\n";
+                break;
+            case 2:
+                o << "      R[" << ks << "] = __fmul2_rn(R[" << ks << "], " << f << "); I[" << ks << "] = __fmul2_rn(I["
+                  << ks << "], " << f << ");\n";
+                break;
+            default:  // -i (R + iI) = I - iR
+                o << "      { const float2 t = I[" << ks << "]; I[" << ks << "] = __fmul2_rn(R[" << ks << "], " << f
+                  << "); R[" << ks << "] = " << (ws == 1.0 ? "t" : "__fmul2_rn(t, " + fp + ")") << "; }\n";
+                break;
+            }
+        }
+        if (R.flags & 2) {
+            for (int k = 0; k < 8; k++)
+                o << "      *reinterpret_cast<float4 *>(psi + (xf | " << hex64(slot_sum(R, k, gbit))
+                  << ")) = make_float4(R[" << k << "].x, I[" << k << "].x, R[" << k << "].y, I[" << k << "].y);\n";
+        } else {
+            for (int k = 0; k < 8; k++)
+                o << "      X4[swu ^ " << hex32((uint32_t)slot_sum(R, k, ucol)) << "] = make_float4(R[" << k << "].x, R["
+                  << k << "].y, I[" << k << "].x, I[" << k << "].y);\n";
+        }
+        o << "    }\n";
+    }
+    o << "  }\n}\n\n";
+    return o.str();
+}
+
 std::string cache_dir() {
     const char *e = getenv("SD_JIT_CACHE");
     if (e && *e) return e;
@@ -607,7 +875,8 @@ std::string source_range(const Schedule &S, int n, bool dbl_state, int first, in
     src << "#include \"dev_types.h\"\n#include \"tile_device.cuh\"\n"
         << "typedef " << (dbl_state ? "double" : "float") << " T;\n"
         << "typedef " << (dbl_state ? "double2" : "float2") << " A;\n\n";
-    for (int p = first; p < last; p++) src << gen_pass(S, p, n, dbl_state);
+    for (int p = first; p < last; p++)
+        src << (!dbl_state && packed_pass(S, p) ? gen_pass_packed(S, p, n) : gen_pass(S, p, n, dbl_state));
     return src.str();
 }
 

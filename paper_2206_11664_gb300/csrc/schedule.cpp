@@ -44,6 +44,13 @@ uint32_t swizzle_col(int p, int c) {
     return (1u << p) | s;
 }
 
+uint32_t pair_swizzle_col(int p) {
+    const int b = p - 1;   // unit index bit of position p
+    if (b < kPairBankBits) return 1u << b;
+    const uint32_t span = (1u << kPairBankBits) - 1u;
+    return (1u << b) | (1u + (uint32_t)((b - kPairBankBits) % (int)span));
+}
+
 namespace {
 
 void layers(const GroupPlan &gp, std::vector<Gate> &ua, std::vector<Gate> &cn,
@@ -296,8 +303,11 @@ int rank_cols(const std::vector<uint32_t> &cols, int c) {
     return r;
 }
 
-// Lane/warp assignment of the non-register tile positions.
-void assign_layout(DevRound &R, int K, int c, bool global_io) {
+// Lane/warp assignment of the non-register tile positions.  With pin0 the
+// global load/store rounds put positions 1..c-1 on the low lanes (with
+// position 0 in registers, 8 lanes then cover 128 contiguous bytes), and the
+// other rounds choose lanes whose paired-layout columns span its bank bits.
+void assign_layout(DevRound &R, int K, int c, bool global_io, bool pin0) {
     std::vector<int> rest;
     for (int p = 0; p < K; p++) {
         bool isreg = false;
@@ -308,7 +318,26 @@ void assign_layout(DevRound &R, int K, int c, bool global_io) {
     // address (conflict-free shared accesses; coalesced global accesses in
     // load/store rounds, where they are tile positions 0..c-1).
     std::vector<int> lanes;
-    if (global_io) {
+    if (pin0 && global_io) {
+        for (int p = 1; p < c; p++) lanes.push_back(p);
+        for (int p : rest)
+            if ((int)lanes.size() < kLaneBits && p >= c) lanes.push_back(p);
+    } else if (pin0) {
+        std::vector<uint32_t> cols;
+        for (int p : rest) {
+            if ((int)lanes.size() >= kPairBankBits) break;
+            std::vector<uint32_t> t = cols;
+            t.push_back(pair_swizzle_col(p));
+            if (rank_cols(t, kPairBankBits) > rank_cols(cols, kPairBankBits)) {
+                lanes.push_back(p);
+                cols = t;
+            }
+        }
+        for (int p : rest)
+            if ((int)lanes.size() < kLaneBits &&
+                std::find(lanes.begin(), lanes.end(), p) == lanes.end())
+                lanes.push_back(p);
+    } else if (global_io) {
         for (int p = 0; p < c; p++) lanes.push_back(p);
         for (int p : rest)
             if ((int)lanes.size() < kLaneBits && p >= c) lanes.push_back(p);
@@ -337,10 +366,11 @@ void assign_layout(DevRound &R, int K, int c, bool global_io) {
 
 }  // namespace
 
-std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &S) {
+std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &S, bool pin0) {
     S = Schedule{};
     S.K = K;
     S.c = c;
+    S.pin0 = pin0 ? 1 : 0;
     if (K < kRegBits + kLaneBits || K > 13 || n < K) return "invalid tile size";
     const int N = (int)circ.ops.size();
     // Dependencies, per wire.  Diagonal ops commute with each other; CNOTs
@@ -455,7 +485,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             else if (op.kind == OK_CNOT) more_passes = pos_of[op.q2] < 0 || pos_of[op.q] < 0;
         }
         auto deferred = [&](const FlatOp &op) {
-            return more_passes && diag_op_index >= 0 && is_1q(op.kind) && op.q < c;
+            return more_passes && diag_op_index >= 0 && is_1q(op.kind) && op.q < c && !(pin0 && op.q == 0);
         };
         int nr = 0;
         for (;;) {
@@ -464,7 +494,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             // score: (first pending one-qubit op on the position, or INT32_MAX if
             // none is ready -- all its predecessors done -- yet)
             std::vector<std::pair<int, int>> score;
-            for (int p = 0; p < K; p++) {
+            for (int p = pin0 ? 1 : 0; p < K; p++) {
                 if (is_load && p < c) continue;
                 int best = INT32_MAX;
                 for (int j = first; j < N; j++) {
@@ -483,6 +513,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             std::stable_sort(score.begin(), score.end());
             DevRound R{};
             std::vector<int> regs;
+            if (pin0) regs.push_back(0);
             // The low positions (< c) are lanes in the load and store layouts, so
             // their gates need a middle round: when one of them is due, take all
             // low positions with pending gates together, then the most urgent others.
@@ -491,8 +522,10 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             int lows_pending = 0, highs_pending = 0;
             for (auto &sc : score)
                 if (sc.first != INT32_MAX) (sc.second < c ? lows_pending : highs_pending)++;
+            const int free_slots = pin0 ? 3 : 4;
             const bool low_round = !is_load && lows_pending > 0 &&
-                                   ((score[0].first != INT32_MAX && score[0].second < c) || highs_pending <= 4);
+                                   ((score[0].first != INT32_MAX && score[0].second < c) ||
+                                    highs_pending <= free_slots);
             if (low_round)
                 for (auto &sc : score)
                     if (sc.second < c && sc.first != INT32_MAX && (int)regs.size() < 4) regs.push_back(sc.second);
@@ -712,11 +745,14 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
         // -------- the last round stores to global memory
         DevRound &last = S.rounds.back();
         bool store_ok = last.perm < 0;
-        for (int i = 0; i < 4; i++) store_ok &= last.reg_pos[i] >= c;
+        for (int i = pin0 ? 1 : 0; i < 4; i++) store_ok &= last.reg_pos[i] >= c;
         if (!store_ok) {
             DevRound R{};
-            // register positions: the 4 lowest positions >= c
+            // register positions: the 4 lowest positions >= c (with pin0:
+            // position 0 and the 3 lowest positions >= c)
             for (int i = 0; i < 4; i++) R.reg_pos[i] = (uint8_t)(c + i);
+            if (pin0)
+                for (int i = 0; i < 4; i++) R.reg_pos[i] = (uint8_t)(i == 0 ? 0 : c + i - 1);
             R.perm = -1;
             R.op_begin = R.op_end = (int)S.ops.size();
             R.slot_begin = (int)S.slots.size();
@@ -730,7 +766,7 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
         }
         S.rounds.back().flags |= 2;
         for (int r = P.round_begin; r < (int)S.rounds.size(); r++)
-            assign_layout(S.rounds[r], K, c, (S.rounds[r].flags & 3) != 0);
+            assign_layout(S.rounds[r], K, c, (S.rounds[r].flags & 3) != 0, pin0);
         P.n_rounds = (int)S.rounds.size() - P.round_begin;
         P.max_stage = 0;
         P.max_tot = 0;

@@ -125,6 +125,9 @@ void canonicalize_1q(Circuit &c, int n);
 struct Schedule {
     int K = 0;
     int c = 0;            // low qubits that must be lanes for coalesced loads/stores
+    // 1: tile position 0 (qubit 0) is register slot 0 in every round, so that
+    // a thread's amplitudes pair up along it (packed two-amplitude layout).
+    int pin0 = 0;
     std::vector<DevPass> passes;
     std::vector<DevRound> rounds;
     std::vector<DevOp> ops;
@@ -141,10 +144,20 @@ struct Schedule {
 };
 
 // Schedule a circuit on n qubits into tile passes of 2^K amplitudes;
-// c = log2(128 bytes / amplitude size).  Returns "" or an error.
-std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &out);
+// c = log2(128 bytes / amplitude size).  pin0: keep tile position 0 in
+// register slot 0 of every round (see Schedule::pin0).  Returns "" or an
+// error.
+std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &out, bool pin0 = false);
 
 // Swizzle column of tile position p (identity on the low c bits).
 uint32_t swizzle_col(int p, int c);
+
+// Bank bits of the paired exchange layout: 16-byte units of two amplitudes
+// that differ in tile position 0, 8 units per 128-byte row.
+constexpr int kPairBankBits = 3;
+
+// Swizzle column, in units, of tile position p >= 1 in the paired layout
+// (identity on positions 1..kPairBankBits).
+uint32_t pair_swizzle_col(int p);
 
 }  // namespace sd

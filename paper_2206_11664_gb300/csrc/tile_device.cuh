@@ -168,6 +168,40 @@ __device__ __forceinline__ double2 rotate_tw(double2 a, uint64_t t, const double
 
 
 
+// e^{-2 pi i t} (times sc) applied to the two amplitudes of a packed pair
+// (R = their real parts, I = their imaginary parts), for Q0.32 turns t0 and
+// t1: the top 9 bits index tables of cos and sin of 2 pi k/512 (TC, TS); the
+// low 23 bits, exact as the mantissa of a float in [1, 2), give the remaining
+// angle phi < 2 pi/512, whose cosine and sine come from their Taylor series
+// (truncation below 1e-9 relative).  Every step but the table index and the
+// mantissa works on both amplitudes with one packed f32x2 instruction.
+__device__ __forceinline__ void rotate_pair32(float2 &R, float2 &I, uint32_t t0, uint32_t t1,
+                                              const float *__restrict__ TC, const float *__restrict__ TS, float sc) {
+    const uint32_t i0 = t0 >> 23, i1 = t1 >> 23;
+    const float2 ec = make_float2(TC[i0], TC[i1]);
+    const float2 es = make_float2(TS[i0], TS[i1]);
+    const float k = (float)(6.283185307179586 / 512.0);
+    const float2 f = make_float2(__uint_as_float(0x3f800000u | (t0 & 0x7fffffu)),
+                                 __uint_as_float(0x3f800000u | (t1 & 0x7fffffu)));
+    const float2 phi = __ffma2_rn(f, make_float2(k, k), make_float2(-k, -k));   // (f - 1) 2 pi/512
+    const float2 p2 = __fmul2_rn(phi, phi);
+    const float2 cp = __ffma2_rn(p2, __ffma2_rn(p2, make_float2(1.0f / 24.0f, 1.0f / 24.0f), make_float2(-0.5f, -0.5f)),
+                                 make_float2(1.0f, 1.0f));
+    const float2 sp = __fmul2_rn(phi, __ffma2_rn(p2, make_float2(-1.0f / 6.0f, -1.0f / 6.0f), make_float2(1.0f, 1.0f)));
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    // C + iS = e^{2 pi i k/512} (cp + i sp) = e^{2 pi i t}
+    float2 C = __ffma2_rn(es, __fmul2_rn(sp, m1), __fmul2_rn(ec, cp));
+    float2 S = __ffma2_rn(ec, sp, __fmul2_rn(es, cp));
+    if (sc != 1.0f) {
+        C = __fmul2_rn(C, make_float2(sc, sc));
+        S = __fmul2_rn(S, make_float2(sc, sc));
+    }
+    const float2 nS = __fmul2_rn(S, m1);
+    const float2 r = __ffma2_rn(I, S, __fmul2_rn(R, C));    // re C + im S
+    I = __ffma2_rn(R, nS, __fmul2_rn(I, C));                // im C - re S
+    R = r;
+}
+
 // Rounding bias of the class totals: complex64 passes finish the angle in
 // Q0.32 (the high word of G + 2^31 is G rounded to 2^-32 turns, the float
 // rotation's own resolution); complex128 passes keep Q0.64.

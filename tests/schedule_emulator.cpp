@@ -31,7 +31,8 @@
 // Usage: schedule_emulator <input> <output>, or <input> - to schedule only
 // (the input then ends before the state, and nothing is executed).
 // The input is binary, in this order: int32 n, int64 m, int32 skip_rule,
-// int32 K, int32 c, int32 order, int32 reps, int64 steps, float64 dt,
+// int32 K, int32 c (plus 16 to pin tile position 0 to register slot 0, the
+// paired complex64 schedule), int32 order, int32 reps, int64 steps, float64 dt,
 // uint64 x[m], uint64 z[m], float64 coeffs[m], complex128 psi[2^n]. The
 // output is complex128 psi[2^n].
 #include <cmath>
@@ -199,13 +200,19 @@ struct BankStats {
     long rounds = 0, short_lanes = 0, perm_rounds = 0, short_perm = 0;
 };
 
+// With a paired schedule the exchange moves 16-byte pairs of amplitudes
+// (paired swizzle, kPairBankBits bank bits) and a quarter warp's 8 lanes must
+// span those bits.
 void bank_stats(const Schedule &S, BankStats &b) {
     const int c = S.c;
     for (const DevRound &R : S.rounds) {
         std::vector<uint32_t> cols;
-        for (int i = 0; i < 5; i++) cols.push_back(swizzle_col(R.lane_pos[i], c));
+        if (S.pin0)
+            for (int i = 0; i < 3; i++) cols.push_back(pair_swizzle_col(R.lane_pos[i]));
+        else
+            for (int i = 0; i < 5; i++) cols.push_back(swizzle_col(R.lane_pos[i], c));
         b.rounds++;
-        if (bank_rank(cols, c) < c) b.short_lanes++;
+        if (S.pin0 ? bank_rank(cols, kPairBankBits) < kPairBankBits : bank_rank(cols, c) < c) b.short_lanes++;
         if (R.perm >= 0) {
             const DevPerm &pm = S.perms[R.perm];
             std::vector<uint32_t> pc;
@@ -221,11 +228,18 @@ void bank_stats(const Schedule &S, BankStats &b) {
     }
 }
 
-// Schedules a circuit (one-qubit runs canonicalised first).
-bool schedule(Circuit circ, int n, int K, int c, Schedule &S) {
+// Schedules a circuit (one-qubit runs canonicalised first).  A paired
+// schedule must keep tile position 0 in register slot 0 of every round.
+bool schedule(Circuit circ, int n, int K, int c, bool pin0, Schedule &S) {
     canonicalize_1q(circ, n);
-    const std::string e = schedule_circuit(circ, n, K, c, S);
+    const std::string e = schedule_circuit(circ, n, K, c, S, pin0);
     if (!e.empty()) std::fprintf(stderr, "schedule: %s\n", e.c_str());
+    if (pin0)
+        for (const DevRound &R : S.rounds)
+            if (R.reg_pos[0] != 0) {
+                std::fprintf(stderr, "schedule: a round without position 0 in slot 0\n");
+                return false;
+            }
     return e.empty();
 }
 
@@ -242,6 +256,8 @@ int main(int argc, char **argv) {
               std::fread(&K, 4, 1, f) == 1 && std::fread(&c, 4, 1, f) == 1 && std::fread(&order, 4, 1, f) == 1 &&
               std::fread(&reps, 4, 1, f) == 1 && std::fread(&steps, 8, 1, f) == 1 && std::fread(&dt, 8, 1, f) == 1;
     ok = ok && reps >= 1;
+    const bool pin0 = (c >> 4) & 1;
+    c &= 15;
     std::vector<uint64_t> x(m), z(m);
     std::vector<double> coef(m);
     std::vector<cd> psi(run ? (size_t)1 << n : 0);
@@ -312,7 +328,7 @@ int main(int argc, char **argv) {
     BankStats banks;
     std::vector<Schedule> scheds(segs.size());
     for (size_t i = 0; i < segs.size(); i++) {
-        if (!schedule(segs[i].first, n, K, c, scheds[i])) return 1;
+        if (!schedule(segs[i].first, n, K, c, pin0, scheds[i])) return 1;
         bank_stats(scheds[i], banks);
         Emulator em{n, scheds[i], psi};
         if (run)

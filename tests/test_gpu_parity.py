@@ -46,9 +46,9 @@ def _rand_state(rng, n):
 
 
 def _check(sd, h, psi0, dt_, steps, order, dtype, skip_rule=-1, tile_bits=0, pauli=False, jit=0,
-           grouping=0):
+           grouping=0, layout=0):
     sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(skip_rule=skip_rule, tile_bits=tile_bits, jit=jit,
-                                                grouping=grouping)
+                                                grouping=grouping, layout=layout)
     groups = P.partition(h.x, h.z, grouping, h.c)
     ref = oracle.evolve(h, psi0, dt_, steps, order, groups)
     t = _dev(psi0, dtype)
@@ -461,6 +461,54 @@ def test_jit_heisenberg_and_random(sd, dtype):
     h2 = random_klocal(15, 50, rng, weights=(2, 3, 4))
     _check(sd, h2, _rand_state(rng, 15), 0.05, 2, 2, dtype, skip_rule=0, jit=1)
     _check(sd, h2, _rand_state(rng, 15), 0.05, 2, 1, dtype, tile_bits=11, jit=1)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_paired_layout(sd, order):
+    """Complex64 passes compiled at run time in the paired layout (qubit 0
+    kept in registers, amplitudes packed in f32x2 pairs) against the oracle:
+    Hadamard-type layers in 4-step blocks (Heisenberg), CNOT permutations and
+    S/CZ layers (random k-local with skip rule 0, whose passes with such
+    rounds keep the plain code inside a paired schedule), a 120-term diagonal
+    group (fully connected Ising), and a smaller tile size."""
+    h = heisenberg_lattice(4, 4)
+    _check(sd, h, basis_state(16, neel_index(4, 4)), 0.02, 6, order, "c64", jit=1, layout=1)
+    rng = np.random.default_rng(67 + order)
+    h2 = random_klocal(15, 50, rng, weights=(2, 3, 4))
+    for rule in (0, 2):
+        _check(sd, h2, _rand_state(rng, 15), 0.05, 2, order, "c64", skip_rule=rule, jit=1, layout=1)
+    _check(sd, h2, _rand_state(rng, 15), 0.05, 3, order, "c64", tile_bits=11, jit=1, layout=1)
+    h3 = tfim_fully_connected(16, rng)
+    _check(sd, h3, _rand_state(rng, 16), 0.02, 5, order, "c64", jit=1, layout=1)
+
+
+def test_autotune_shape(sd, tmp_path):
+    """The shape autotuner times tile sizes in both layouts of the run-time
+    complex64 passes, keeps the fastest, stores it in a JSON cache that a
+    second simulator applies without timing, and the tuned shape still
+    matches the oracle."""
+    import torch
+    h = heisenberg_lattice(4, 5)                      # n = 20: passes compiled at run time
+    cache = str(tmp_path / "shapes.json")
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    res = sim.autotune_shape(sd.C64, 0.02, steps=4, order=1, kmin=12, kmax=13, cache=cache)
+    assert not res["cached"]
+    ms = {tuple(int(v) for v in k.split(",")): t for k, t in res["ms_per_step"].items()}
+    assert {lay for _, lay in ms} == {-1, 1} and all(t > 0 for t in ms.values())
+    best = (res["tile_bits"], res["layout"])
+    assert best in ms and ms[best] == min(ms.values())
+    assert sim.schedule_stats(sd.C64, 1)["tile_bits"] == res["tile_bits"]
+    again = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    res2 = again.autotune_shape(sd.C64, 0.02, steps=4, order=1, kmin=12, kmax=13, cache=cache)
+    assert res2["cached"] and (res2["tile_bits"], res2["layout"]) == best
+    assert again.schedule_stats(sd.C64, 1)["tile_bits"] == res["tile_bits"]
+    rng = np.random.default_rng(68)
+    psi0 = _rand_state(rng, h.n)
+    ref = oracle.evolve(h, psi0, 0.02, 5, 1, P.greedy_partition(h.x, h.z))
+    for s_ in (sim, again):
+        t = _dev(psi0, "c64")
+        s_.evolve(t, 0.02, 5, 1)
+        assert np.linalg.norm(_host(t) - ref) <= TOL["c64"]
 
 
 def test_jit_complex128_fixed_point(sd):

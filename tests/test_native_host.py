@@ -240,6 +240,38 @@ def test_argument_validation_of_the_other_entry_points(sd):
     assert lib.sd_prepare_batch(hs, ps, -1, N.SD_C64, 0.1, 1, 1) == N.SD_EINVAL
     assert lib.sd_prepare_batch(hs, ps, 70000, N.SD_C64, 0.1, 1, 1) == N.SD_EINVAL
     assert lib.sd_evolve_host(sim._h, None, None, N.SD_C64, 0.1, 1, 1, None) == N.SD_EINVAL
+    tr = N.TuneResult()
+    assert lib.sd_autotune_shape(unplanned._h, N.SD_C64, 0.1, 4, 1, 11, 13, ctypes.byref(tr)) == N.SD_ENOPLAN
+    assert lib.sd_autotune_shape(sim._h, N.SD_C64, 0.1, 4, 1, 11, 13, None) == N.SD_EINVAL
+    for kmin, kmax in ((8, 13), (12, 14), (13, 12)):
+        assert lib.sd_autotune_shape(sim._h, N.SD_C64, 0.1, 4, 1, kmin, kmax, ctypes.byref(tr)) == N.SD_EINVAL
+    assert lib.sd_autotune_shape(sim._h, N.SD_C64, 0.1, 4, 3, 11, 13, ctypes.byref(tr)) == N.SD_EINVAL
+    assert lib.sd_autotune_shape(sim._h, 7, 0.1, 4, 1, 11, 13, ctypes.byref(tr)) == N.SD_EINVAL
+    for bad in (-2, 2):
+        o = N.PlanOpts(-1, 0, 0, 0, bad)
+        assert lib.sd_plan(sim._h, ctypes.byref(o)) == N.SD_EINVAL
+
+
+def test_paired_layout_schedules(sd, tmp_path, monkeypatch):
+    """The paired layout (sd_plan_opts.layout = 1) schedules complex64
+    programs compiled at run time with qubit 0 in registers: the benchmark
+    calls keep their pass counts, complex128 and interpreter-only programs
+    are unaffected, and the paired kernels of the benchmark programs compile
+    with NVRTC for sm_103a on the host."""
+    monkeypatch.setenv("SD_JIT_CACHE", str(tmp_path))
+    h = heisenberg_lattice(5, 6)
+    plain = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    paired = sd.Simulator(h.n, h.x, h.z, h.c).plan(layout=1)
+    for steps in (1, 4, 20):
+        for dt in (sd.C64, sd.C128):
+            assert paired.count_passes(dt, 1, steps) == plain.count_passes(dt, 1, steps)
+    assert paired.schedule_stats(sd.C64, 1)["rounds_per_step"] > plain.schedule_stats(sd.C64, 1)["rounds_per_step"]
+    assert paired.schedule_stats(sd.C128, 1) == plain.schedule_stats(sd.C128, 1)
+    assert paired.precompile(sd.C64, 4, 1) >= 1
+    small = heisenberg_lattice(3, 5)            # n = 15: interpreter only, layout has no effect
+    a = sd.Simulator(small.n, small.x, small.z, small.c).plan()
+    b = sd.Simulator(small.n, small.x, small.z, small.c).plan(layout=1)
+    assert a.schedule_stats(sd.C64, 1) == b.schedule_stats(sd.C64, 1)
 
 
 def test_noalloc_argument_validation(sd):
@@ -324,6 +356,7 @@ def _ctype_of(decl):
              "uint64_t*": N.P_u64, "double*": N.P_dbl, "char**": ctypes.POINTER(ctypes.c_char_p),
              "sd_plan_opts*": ctypes.POINTER(N.PlanOpts), "sd_plan_view*": ctypes.POINTER(N.PlanView),
              "sd_schedule_stats*": ctypes.POINTER(N.ScheduleStats), "int*": ctypes.POINTER(N.c_int),
+             "sd_tune_result*": ctypes.POINTER(N.TuneResult),
              "int64_t*": ctypes.POINTER(N.c_i64), "void**": ctypes.POINTER(N.c_vp),
              "sd_ctx**const": ctypes.POINTER(N.c_vp)}
     return table[t]
@@ -346,7 +379,7 @@ def test_binding_matches_the_header():
             # device addresses (d_...) are passed as plain addresses
             assert _ctype_of(decl) == a or (device_ptr and a is N.c_vp), (name, decl)
     for cname, pyname in (("sd_plan_opts", "PlanOpts"), ("sd_plan_view", "PlanView"),
-                          ("sd_schedule_stats", "ScheduleStats")):
+                          ("sd_schedule_stats", "ScheduleStats"), ("sd_tune_result", "TuneResult")):
         header_fields = [re.sub(r"\[.*\]", "", d).split()[-1].lstrip("*") for d in structs[cname]]
         assert header_fields == [f[0] for f in getattr(N, pyname)._fields_], cname
 

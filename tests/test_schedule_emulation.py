@@ -34,10 +34,10 @@ def emulator(tmp_path_factory):
     return exe
 
 
-def _run(exe, tmp_path, h, psi0, dt, steps, order, skip, K, c, reps=1):
+def _run(exe, tmp_path, h, psi0, dt, steps, order, skip, K, c, reps=1, pin0=False):
     inp, out = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(inp, "wb") as f:
-        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c, order, reps, steps, dt))
+        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c + 16 * pin0, order, reps, steps, dt))
         f.write(np.ascontiguousarray(h.x, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.z, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.c, dtype=np.float64).tobytes())
@@ -66,14 +66,15 @@ def test_schedule_matches_oracle(emulator, tmp_path, case, skip):
     rng = np.random.default_rng(700 + 10 * case + skip)
     h = CASES[case][1](rng)
     groups = P.greedy_partition(h.x, h.z)
-    for order, K, c in ((1, 9, 4), (2, 10, 3), (1, 11, 4)):
+    for order, K, c, pin0 in ((1, 9, 4, False), (2, 10, 3, False), (1, 11, 4, False), (2, 10, 4, True),
+                              (1, 11, 4, True)):
         if K > h.n:
             continue
         psi0 = _rand(rng, h.n)
-        got = _run(emulator, tmp_path, h, psi0, 0.05, 2, order, skip, K, c)
+        got = _run(emulator, tmp_path, h, psi0, 0.05, 2, order, skip, K, c, pin0=pin0)
         ref = oracle.evolve(h, psi0, 0.05, 2, order, groups)
         err = np.linalg.norm(got - ref)
-        assert err < 1e-10, (CASES[case][0], skip, order, K, err)
+        assert err < 1e-10, (CASES[case][0], skip, order, K, pin0, err)
 
 
 @pytest.mark.parametrize("order", [1, 2])
@@ -87,19 +88,19 @@ def test_blocks_at_the_default_tile_sizes(emulator, tmp_path, order):
              jw_like(n=14, m=300, rng=rng)]
     for h in cases:
         groups = P.greedy_partition(h.x, h.z)
-        for K, c in ((13, 4), (12, 3)):
+        for K, c, pin0 in ((13, 4, False), (12, 3, False), (13, 4, True)):
             psi0 = _rand(rng, h.n)
-            got = _run(emulator, tmp_path, h, psi0, 0.03, 6, order, 2, K, c, reps=4)
+            got = _run(emulator, tmp_path, h, psi0, 0.03, 6, order, 2, K, c, reps=4, pin0=pin0)
             ref = oracle.evolve(h, psi0, 0.03, 6, order, groups)
             err = np.linalg.norm(got - ref)
-            assert err < 1e-10, (h.n, h.m, order, K, err)
+            assert err < 1e-10, (h.n, h.m, order, K, pin0, err)
 
 
-def _schedule_only(exe, tmp_path, h, order, K, c, steps, reps, skip=2):
+def _schedule_only(exe, tmp_path, h, order, K, c, steps, reps, skip=2, pin0=False):
     """Passes of a call and the bank statistics of its rounds, without a state."""
     inp = tmp_path / "sched.bin"
     with open(inp, "wb") as f:
-        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c, order, reps, steps, 0.02))
+        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c + 16 * pin0, order, reps, steps, 0.02))
         f.write(np.ascontiguousarray(h.x, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.z, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.c, dtype=np.float64).tobytes())
@@ -119,9 +120,10 @@ def test_benchmark_rounds_are_free_of_bank_conflicts(emulator, tmp_path):
     steps need no tile permutations."""
     for (rows, cols, corners), passes in (((5, 6, False), 125), ((6, 6, True), 185)):
         h = heisenberg_lattice(rows, cols, drop_corners=corners)
-        for K, c in ((13, 4), (12, 3)):
-            got, rounds, short_lanes, perm_rounds, _ = _schedule_only(emulator, tmp_path, h, 1, K, c, 20, 4)
-            assert got == passes
+        for K, c, pin0 in ((13, 4, False), (12, 3, False), (13, 4, True)):
+            got, rounds, short_lanes, perm_rounds, _ = _schedule_only(emulator, tmp_path, h, 1, K, c, 20, 4,
+                                                                      pin0=pin0)
+            assert got == passes, (rows, cols, K, pin0, got)
             assert rounds > 0 and short_lanes == 0 and perm_rounds == 0
 
 
