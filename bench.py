@@ -367,7 +367,8 @@ def main():
                       "l2": "state 8 GiB > 129 MB L2, no flush needed" if n == 30 else "small",
                       "parallelism": f"replicas x{ws}", "tile_bits": st64["tile_bits"],
                       "autotune": ({"tile_bits": tuned["tile_bits"], "layout": tuned["layout"],
-                                    "ms_per_step (K,layout)": tuned["ms_per_step"]} if tuned else None),
+                                    "prefetch": tuned["prefetch"],
+                                    "ms_per_step (K,layout,prefetch)": tuned["ms_per_step"]} if tuned else None),
                       "passes_per_step": launches / args.steps,
                       "passes_per_single_step": st64["passes_per_step"]},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -98,16 +98,24 @@ typedef struct {
      * register round in some passes); 0 = default (plain, or what
      * sd_autotune_shape chose).  Complex128 passes ignore it. */
     int layout;
-    int reserved[3];
+    /* Tiles in flight in the passes compiled at run time: 1 = one prefetch
+     * buffer (the next tile is loaded after a barrier that follows the load
+     * of the current one); 2 = two buffers (no such barrier; 64 KB more
+     * shared memory, used only where it fits); 0 = default (1, or what
+     * sd_autotune_shape chose). */
+    int prefetch;
+    int reserved[2];
 } sd_plan_opts;
 
 /* Result of sd_autotune_shape: the shape kept, and milliseconds per step
- * for tile sizes K = 9..13 in the plain (index 0) and paired (index 1)
- * layouts, 0 where not run. */
+ * for tile sizes K = 9..13 (last index) in the plain layout with one and two
+ * prefetch buffers (first index 0, 1) and in the paired layout with one and
+ * two (2, 3); 0 where not run. */
 typedef struct {
     int best_k;
     int best_layout;          /* -1 plain, 1 paired; 0 on the on-chip path */
-    double ms[2][5];
+    int best_prefetch;        /* 1 or 2 prefetch buffers; 0 on the on-chip path */
+    double ms[4][5];
 } sd_tune_result;
 
 /* Read-only view of a plan; pointers stay valid until the next sd_plan or
@@ -200,10 +208,11 @@ sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int
                       int kmax, int *best_k, double *times_ms);
 
 /* Shape autotuner: as sd_autotune, over tile sizes K = kmin..kmax and, for
- * complex64 states whose passes are compiled at run time, over both
- * register layouts (plain and paired, see sd_plan_opts.layout); the
- * fastest (K, layout) is kept for this dtype until the next sd_plan (a tile
- * size or layout given to sd_plan overrides the tuned one).  Synchronous;
+ * states whose passes are compiled at run time, over the prefetch depth (1
+ * or 2 buffers, see sd_plan_opts.prefetch) and, for complex64, both
+ * register layouts (plain and paired, see sd_plan_opts.layout); the fastest
+ * shape is kept for this dtype until the next sd_plan (a tile size, layout
+ * or prefetch depth given to sd_plan overrides the tuned one).  Synchronous;
  * scratch state and errors as for sd_autotune; *out may not be NULL. */
 sd_status sd_autotune_shape(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin,
                             int kmax, sd_tune_result *out);

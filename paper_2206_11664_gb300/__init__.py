@@ -128,11 +128,12 @@ class Simulator:
             pass
 
     # ------------------------------------------------------------ planning
-    def plan(self, skip_rule=-1, tile_bits=0, jit=0, grouping=0, layout=0):
+    def plan(self, skip_rule=-1, tile_bits=0, jit=0, grouping=0, layout=0, prefetch=0):
         """Host planning.  jit: 0 automatic, 1 always, -1 never; grouping:
         0 first fit, 1 largest first, 2 DSATUR, 3 by |c|; layout of the
-        complex64 run-time passes: 0 default, -1 plain, 1 paired (see sd.h)."""
-        o = N.PlanOpts(skip_rule, tile_bits, jit, grouping, layout)
+        complex64 run-time passes: 0 default, -1 plain, 1 paired; prefetch
+        buffers of the run-time passes: 0 default, 1 or 2 (see sd.h)."""
+        o = N.PlanOpts(skip_rule, tile_bits, jit, grouping, layout, prefetch)
         self._check(self._lib.sd_plan(self._h, ctypes.byref(o)))
         return self
 
@@ -192,7 +193,7 @@ class Simulator:
         """Time tile sizes kmin..kmax and, for complex64 passes compiled at
         run time, both register layouts (sd_autotune_shape); the fastest
         shape is kept for `dtype`.  Returns {"tile_bits", "layout",
-        "ms_per_step": {(K, layout): ms}}.  With `cache` (a JSON file path),
+        "prefetch", "ms_per_step": {"K,layout,prefetch": ms}}.  With `cache` (a JSON file path),
         a shape stored there for this Hamiltonian, dtype, order and dt is
         applied by re-planning with it instead of timing, and a newly timed
         shape is stored."""
@@ -214,7 +215,7 @@ class Simulator:
                     known = json.load(f)
                 if key in known:
                     got = known[key]
-                    self.plan(tile_bits=got["tile_bits"], layout=got["layout"])
+                    self.plan(tile_bits=got["tile_bits"], layout=got["layout"], prefetch=got["prefetch"])
                     got = dict(got)
                     got["cached"] = True
                     return got
@@ -222,17 +223,19 @@ class Simulator:
         self._check(self._lib.sd_autotune_shape(self._h, dtype, float(dt), int(steps), int(order), kmin, kmax,
                                                 ctypes.byref(r)))
         ms = {}
-        for li, lay in ((0, -1), (1, 1)):
+        for li, (lay, pf) in enumerate(((-1, 1), (-1, 2), (1, 1), (1, 2))):
             for k in range(kmin, kmax + 1):
                 if r.ms[li][k - 9] > 0:
-                    ms[f"{k},{lay}"] = float(r.ms[li][k - 9])
-        out = {"tile_bits": r.best_k, "layout": r.best_layout, "ms_per_step": ms, "cached": False}
+                    ms[f"{k},{lay},{pf}"] = float(r.ms[li][k - 9])
+        out = {"tile_bits": r.best_k, "layout": r.best_layout, "prefetch": r.best_prefetch, "ms_per_step": ms,
+               "cached": False}
         if key is not None and r.best_k > 0:
             known = {}
             if os.path.exists(cache):
                 with open(cache) as f:
                     known = json.load(f)
-            known[key] = {"tile_bits": r.best_k, "layout": r.best_layout, "ms_per_step": ms}
+            known[key] = {"tile_bits": r.best_k, "layout": r.best_layout, "prefetch": r.best_prefetch,
+                          "ms_per_step": ms}
             tmp = f"{cache}.tmp{os.getpid()}"
             with open(tmp, "w") as f:
                 json.dump(known, f, indent=1, sort_keys=True)

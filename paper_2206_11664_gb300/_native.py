@@ -22,11 +22,11 @@ STATUS_NAMES = {0: "SD_OK", 1: "SD_EINVAL", 2: "SD_ENOMEM", 3: "SD_ECUDA", 4: "S
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("skip_rule", c_int), ("tile_bits", c_int), ("jit", c_int), ("grouping", c_int),
-                ("layout", c_int), ("reserved", c_int * 3)]
+                ("layout", c_int), ("prefetch", c_int), ("reserved", c_int * 2)]
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("best_k", c_int), ("best_layout", c_int), ("ms", (c_dbl * 5) * 2)]
+    _fields_ = [("best_k", c_int), ("best_layout", c_int), ("best_prefetch", c_int), ("ms", (c_dbl * 5) * 4)]
 
 
 class PlanView(ctypes.Structure):

@@ -72,6 +72,8 @@ struct sd_ctx {
     int jit_opt = 0;
     int layout_opt = 0;        // sd_plan_opts.layout
     int tuned_layout = 0;      // complex64 layout chosen by sd_autotune_shape (1 paired, -1 plain)
+    int prefetch_opt = 0;      // sd_plan_opts.prefetch
+    int tuned_prefetch[2] = {0, 0};   // prefetch buffers chosen by sd_autotune_shape (per dtype)
     std::string jit_note;    // why the last program did not use run-time specialisation
     // plan view storage
     std::vector<int64_t> v_goff, v_gterms, v_gateoff;
@@ -83,6 +85,7 @@ struct sd_ctx {
     int num_sms = 0;
     std::map<std::tuple<int, int, int, double>, std::unique_ptr<Program>> programs;
     std::map<std::tuple<int, int, int>, std::unique_ptr<Program>> cliff_programs;   // (dtype, group, fwd)
+    std::map<std::tuple<int, int, int>, std::unique_ptr<Program>> transition_programs;   // (dtype, from, to)
     std::map<std::pair<int, double>, GradGroup> grad_groups;
     std::vector<void *> grad_allocs;
     double *d_partial = nullptr;
@@ -100,6 +103,7 @@ struct sd_ctx {
         batch_purge(this);
         for (auto &kv : programs) free_program(*kv.second);
         for (auto &kv : cliff_programs) free_program(*kv.second);
+        for (auto &kv : transition_programs) free_program(*kv.second);
         for (void *a : grad_allocs) cudaFree(a);
         cudaFree(d_partial);
         cudaFree(d_scalar);
@@ -241,6 +245,14 @@ bool jit_wanted(const sd_ctx *ctx, bool allow_jit, int64_t passes) {
     return mode > 0 || (mode == 0 && allow_jit && ctx->n >= 20 && passes <= kJitMaxPasses);
 }
 
+// Prefetch buffers of the run-time passes: sd_plan's choice, else the tuned
+// one, else one.
+int prefetch_buffers(const sd_ctx *ctx, bool dbl) {
+    if (ctx->prefetch_opt > 0) return ctx->prefetch_opt;
+    const int t = ctx->tuned_prefetch[dbl ? 1 : 0];
+    return t > 0 ? t : 1;
+}
+
 // With the paired layout, complex64 programs that will probably be compiled
 // at run time are scheduled with tile position 0 pinned to register slot 0,
 // which the paired pass code needs (the interpreter runs such schedules as
@@ -290,6 +302,7 @@ sd_status build_program(sd_ctx *ctx, const Circuit &circ_in, bool dbl, Program &
     Schedule S;
     sd_status ss = schedule_for(ctx, circ, dbl, S, pin0_wanted(ctx, dbl, allow_jit));
     if (ss != SD_OK) return ss;
+    S.prefetch = prefetch_buffers(ctx, dbl);
     DevSchedule &D = P.sched;
     DevTables tabs;
     if ((ss = device_tables(ctx, tabs)) != SD_OK) return ss;
@@ -681,6 +694,36 @@ bool program_empty(const Program &P) {
     return P.onchip ? P.circ.n_ops == 0 : P.sched.n_passes == 0;
 }
 
+// Program of the change of frame between two group exponentials of the
+// adjoint sweep: C_b C_a^dag (leave group a's diagonal frame, enter group
+// b's), one circuit so that the one-qubit gates of both merge.
+sd_status get_transition(sd_ctx *ctx, bool dbl, int a, int b, Program *&out) {
+    auto key = std::make_tuple((int)dbl, a, b);
+    auto it = ctx->transition_programs.find(key);
+    if (it != ctx->transition_programs.end()) {
+        out = it->second.get();
+        return SD_OK;
+    }
+    Circuit c;
+    if (a != b) {
+        append_clifford(ctx->plan, a, false, c);
+        append_clifford(ctx->plan, b, true, c);
+    }
+    auto P = std::make_unique<Program>();
+    if (c.ops.empty()) {
+        P->onchip = false;   // empty: nothing to run
+    } else {
+        sd_status s = build_program(ctx, c, dbl, *P);
+        if (s != SD_OK) {
+            free_program(*P);
+            return s;
+        }
+    }
+    out = P.get();
+    ctx->transition_programs[key] = std::move(P);
+    return SD_OK;
+}
+
 sd_status get_grad_group(sd_ctx *ctx, int g, double f, double dt, GradGroup *&out) {
     auto key = std::make_pair(g, f);
     auto it = ctx->grad_groups.find(key);
@@ -796,14 +839,16 @@ sd_status sd_set_coeffs(sd_ctx *ctx, const double *coeffs) {
 
 sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
-    int rule = 2, tb = 0, jit = 0, grouping = 0, layout = 0;
+    int rule = 2, tb = 0, jit = 0, grouping = 0, layout = 0, prefetch = 0;
     if (opts) {
         rule = opts->skip_rule < 0 ? 2 : opts->skip_rule;
         tb = opts->tile_bits;
         jit = opts->jit;
         grouping = opts->grouping;
         layout = opts->layout;
+        prefetch = opts->prefetch;
         if (layout < -1 || layout > 1) return fail(ctx, SD_EINVAL, "layout must be -1, 0 or 1");
+        if (prefetch < 0 || prefetch > 2) return fail(ctx, SD_EINVAL, "prefetch must be 0, 1 or 2");
         if (rule > 2) return fail(ctx, SD_EINVAL, "skip_rule must be -1, 0, 1 or 2");
         if (tb != 0 && (tb < 9 || tb > 13)) return fail(ctx, SD_EINVAL, "tile_bits must be 0 or 9..13");
         if (grouping < 0 || grouping > 3) return fail(ctx, SD_EINVAL, "grouping must be 0, 1, 2 or 3");
@@ -816,6 +861,8 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     ctx->programs.clear();
     for (auto &kv : ctx->cliff_programs) free_program(*kv.second);
     ctx->cliff_programs.clear();
+    for (auto &kv : ctx->transition_programs) free_program(*kv.second);
+    ctx->transition_programs.clear();
     for (void *a : ctx->grad_allocs) cudaFree(a);
     ctx->grad_allocs.clear();
     ctx->grad_groups.clear();
@@ -825,6 +872,8 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
     ctx->jit_opt = jit;
     ctx->layout_opt = layout;
     ctx->tuned_layout = 0;
+    ctx->prefetch_opt = prefetch;
+    ctx->tuned_prefetch[0] = ctx->tuned_prefetch[1] = 0;
     ctx->planned = true;
     // plan view
     ctx->v_goff.assign(1, 0);
@@ -911,7 +960,8 @@ namespace {
 // 1 paired), after one untimed call that builds and compiles the programs;
 // keeps the fastest pair for the dtype.  ms[l][K - 9] receives ms per step.
 sd_status autotune_impl(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin, int kmax,
-                        const std::vector<int> &layouts, int *best_k, int *best_layout, double ms[2][5]) {
+                        const std::vector<std::pair<int, int>> &shapes, int *best_k, int *best_layout,
+                        int *best_prefetch, double ms[4][5]) {
     if (!ctx) return fail(nullptr, SD_EINVAL, "null context");
     if (!ctx->planned) return fail(ctx, SD_ENOPLAN, "sd_plan has not been called");
     if (dtype != SD_C64 && dtype != SD_C128) return fail(ctx, SD_EINVAL, "dtype must be SD_C64 or SD_C128");
@@ -921,10 +971,11 @@ sd_status autotune_impl(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, i
         return fail(ctx, SD_EINVAL, "tile sizes must satisfy 9 <= kmin <= kmax <= 13");
     const bool dbl = dtype == SD_C128;
     const int d = dbl ? 1 : 0;
-    for (int l = 0; l < 2; l++)
+    for (int l = 0; l < 4; l++)
         for (int k = 0; k < 5; k++) ms[l][k] = 0.0;
     *best_k = 0;
     *best_layout = 0;
+    *best_prefetch = 0;
     sd_status s = ensure_device(ctx);
     if (s != SD_OK) return s;
     if (use_onchip(ctx, dbl)) return SD_OK;   // nothing to tune: one launch runs every step
@@ -941,8 +992,8 @@ sd_status autotune_impl(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, i
     }
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const int saved = ctx->tuned_k[d], saved_layout = ctx->tuned_layout;
-    int best = 0, best_l = 0;
+    const int saved = ctx->tuned_k[d], saved_layout = ctx->tuned_layout, saved_pf = ctx->tuned_prefetch[d];
+    int best = 0, best_l = 0, best_pf = 0;
     double best_ms = 0.0;
     s = SD_OK;
     cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -950,8 +1001,10 @@ sd_status autotune_impl(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, i
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(scratch, 0, bytes, st);
     if (ce != cudaSuccess) s = fail(ctx, SD_ECUDA, std::string("autotune: ") + cudaGetErrorString(ce));
-    for (int L : layouts) {
+    for (const auto &shape : shapes) {
+        const int L = shape.first, PF = shape.second;
         if (!dbl) ctx->tuned_layout = L;
+        ctx->tuned_prefetch[d] = PF;
         for (int K = kmin; K <= kmax && s == SD_OK; K++) {
             if (K > ctx->n) break;
             ctx->tuned_k[d] = K;
@@ -974,10 +1027,11 @@ sd_status autotune_impl(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, i
             float t = 0.f;
             cudaEventElapsedTime(&t, e0, e1);
             const double per = (double)t / (double)steps;
-            ms[L > 0 ? 1 : 0][K - 9] = per;
+            ms[(L > 0 ? 2 : 0) + (PF > 1 ? 1 : 0)][K - 9] = per;
             if (best == 0 || per < best_ms) {
                 best = K;
                 best_l = L;
+                best_pf = PF;
                 best_ms = per;
             }
         }
@@ -989,11 +1043,13 @@ sd_status autotune_impl(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, i
     const bool ok = s == SD_OK && best > 0;
     ctx->tuned_k[d] = ok ? best : saved;
     if (!dbl) ctx->tuned_layout = ok ? best_l : saved_layout;
+    ctx->tuned_prefetch[d] = ok ? best_pf : saved_pf;
     drop_programs();
     if (s != SD_OK) return s;
     if (best == 0) return fail(ctx, SD_EINVAL, "no tile size in the range could be scheduled");
     *best_k = best;
     *best_layout = best_l;
+    *best_prefetch = best_pf;
     return SD_OK;
 }
 
@@ -1001,18 +1057,22 @@ sd_status autotune_impl(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, i
 
 sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int order, int kmin, int kmax,
                       int *best_k, double *times_ms) {
-    int bk = 0, bl = 0;
-    double ms[2][5];
-    // the layout in force (sd_plan's, else the tuned one, else plain) is kept
-    int L = -1;
-    if (ctx) L = ctx->layout_opt != 0 ? ctx->layout_opt : (ctx->tuned_layout != 0 ? ctx->tuned_layout : -1);
+    int bk = 0, bl = 0, bp = 0;
+    double ms[4][5];
+    // the layout and prefetch depth in force (sd_plan's, else the tuned ones,
+    // else plain and one buffer) are kept
+    int L = -1, PF = 1;
+    if (ctx) {
+        L = ctx->layout_opt != 0 ? ctx->layout_opt : (ctx->tuned_layout != 0 ? ctx->tuned_layout : -1);
+        PF = prefetch_buffers(ctx, dtype == SD_C128);
+    }
     if (times_ms && kmin <= kmax)
         for (int k = kmin; k <= kmax; k++) times_ms[k - kmin] = 0.0;
     if (best_k) *best_k = 0;
-    sd_status s = autotune_impl(ctx, dtype, dt, steps, order, kmin, kmax, {L}, &bk, &bl, ms);
+    sd_status s = autotune_impl(ctx, dtype, dt, steps, order, kmin, kmax, {{L, PF}}, &bk, &bl, &bp, ms);
     if (s != SD_OK) return s;
     if (times_ms)
-        for (int k = kmin; k <= kmax; k++) times_ms[k - kmin] = ms[L > 0 ? 1 : 0][k - 9];
+        for (int k = kmin; k <= kmax; k++) times_ms[k - kmin] = ms[(L > 0 ? 2 : 0) + (PF > 1 ? 1 : 0)][k - 9];
     if (best_k) *best_k = bk;
     return SD_OK;
 }
@@ -1021,11 +1081,20 @@ sd_status sd_autotune_shape(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t step
                             int kmax, sd_tune_result *out) {
     if (!out) return fail(ctx, SD_EINVAL, "null result pointer");
     memset(out, 0, sizeof(*out));
-    std::vector<int> layouts{-1};
-    // the paired layout exists for complex64 passes compiled at run time
-    if (ctx && dtype == SD_C64 && ctx->layout_opt == 0 && jit_wanted(ctx, true, 1)) layouts.push_back(1);
-    else if (ctx && dtype == SD_C64 && ctx->layout_opt != 0) layouts.assign(1, ctx->layout_opt);
-    return autotune_impl(ctx, dtype, dt, steps, order, kmin, kmax, layouts, &out->best_k, &out->best_layout, out->ms);
+    // the paired layout exists for complex64 passes compiled at run time, the
+    // second prefetch buffer for passes compiled at run time; options given
+    // to sd_plan are kept
+    std::vector<int> layouts{-1}, depths{1};
+    const bool jit = ctx && jit_wanted(ctx, true, 1);
+    if (ctx && dtype == SD_C64 && ctx->layout_opt != 0) layouts.assign(1, ctx->layout_opt);
+    else if (dtype == SD_C64 && jit) layouts.push_back(1);
+    if (ctx && ctx->prefetch_opt != 0) depths.assign(1, ctx->prefetch_opt);
+    else if (jit) depths.push_back(2);
+    std::vector<std::pair<int, int>> shapes;
+    for (int L : layouts)
+        for (int PF : depths) shapes.push_back({L, PF});
+    return autotune_impl(ctx, dtype, dt, steps, order, kmin, kmax, shapes, &out->best_k, &out->best_layout,
+                         &out->best_prefetch, out->ms);
 }
 
 sd_status sd_evolve_host(sd_ctx *ctx, void *host_state, void *d_work, sd_dtype dtype, double dt,
@@ -1080,6 +1149,7 @@ sd_status sd_precompile(sd_ctx *ctx, sd_dtype dtype, int64_t steps, int order, i
         Schedule S;
         const bool allow = sg.first == 0 || sg.first == 2 || sg.first == 4;
         if ((s = schedule_for(ctx, c, dbl, S, pin0_wanted(ctx, dbl, allow))) != SD_OK) return s;
+        S.prefetch = prefetch_buffers(ctx, dbl);
         if (!jit_wanted(ctx, allow, (int64_t)S.passes.size())) continue;
         int done = 0;
         const std::string e = jit_precompile(S, ctx->n, dbl, &done);
@@ -1242,27 +1312,30 @@ sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt, 
     const int G = (int)ctx->plan.groups.size();
     const int blocks = grad_blocks(ctx->n, ctx->num_sms);
     auto seq = step_sequence(G, order);
+    // Reverse sweep over the group exponentials.  phi and lam stay in the
+    // diagonal frame of the exponential at hand: C_g brings them into the
+    // first one's, each change of group runs one merged program C_b C_a^dag,
+    // and no frame is left at the end (only the gradient is kept).
+    int prev = -1;
     for (int64_t k = 0; k < steps; k++) {
         for (auto it = seq.rbegin(); it != seq.rend(); ++it) {
             const int g = it->first;
-            Program *cf = nullptr, *ci = nullptr;
+            Program *tr = nullptr;
             GradGroup *gg = nullptr;
-            if ((s = get_cliff(ctx, dbl, g, true, cf)) != SD_OK) return s;
-            if ((s = get_cliff(ctx, dbl, g, false, ci)) != SD_OK) return s;
+            if (prev < 0) s = get_cliff(ctx, dbl, g, true, tr);
+            else s = get_transition(ctx, dbl, prev, g, tr);
+            if (s != SD_OK) return s;
             if ((s = get_grad_group(ctx, g, it->second, dt, gg)) != SD_OK) return s;
             if ((s = ensure_partial(ctx, (size_t)blocks * std::max(gg->g.m, 1))) != SD_OK) return s;
-            if (!program_empty(*cf)) {
-                if ((s = run_program(ctx, dbl, *cf, phi, 1, st)) != SD_OK) return s;
-                if ((s = run_program(ctx, dbl, *cf, lam, 1, st)) != SD_OK) return s;
+            if (!program_empty(*tr)) {
+                if ((s = run_program(ctx, dbl, *tr, phi, 1, st)) != SD_OK) return s;
+                if ((s = run_program(ctx, dbl, *tr, lam, 1, st)) != SD_OK) return s;
             }
             CK(launch_grad_diag(dbl, phi, lam, ctx->n, gg->g, gg->masks_f, gg->qinv, nullptr,
                                 ctx->d_partial, blocks, st));
             CK(launch_grad_finalize(ctx->d_partial, blocks, gg->g.m, gg->term_id, gg->factor,
                                     ctx->d_gacc, st));
-            if (!program_empty(*ci)) {
-                if ((s = run_program(ctx, dbl, *ci, phi, 1, st)) != SD_OK) return s;
-                if ((s = run_program(ctx, dbl, *ci, lam, 1, st)) != SD_OK) return s;
-            }
+            prev = g;
         }
     }
     double v = 0.0;

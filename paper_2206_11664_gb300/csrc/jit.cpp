@@ -202,17 +202,19 @@ bool diag_class_used(const DevDiag &d, int u) {
     return d.off[u + 1] > d.off[u] || d.zs[u] >= 0 || (u == 0 && d.cst >= 0);
 }
 
-// Staging of a round's group exponentials for the tile (slot sums, tile
-// constants, class totals), with the barriers around it.  Complex64 passes
-// bias the class totals by 2^31 (rounding to Q0.32 turns), complex128 passes
-// keep Q0.64.
-void emit_round_staging(std::ostringstream &o, const Schedule &S, const DevPass &P, const DevRound &R, int NT,
-                        bool dbl_state) {
-    // Straight-line code only for rounds of modest size: longer code
-    // compiles slowly and gains nothing once the work is spread out.
+// Whether a round's staging is emitted as straight-line code (rounds of
+// modest size: longer code compiles slowly and gains nothing once the work is
+// spread out).
+bool round_inline_stage(const Schedule &S, const DevRound &R) {
     int round_terms = 0;
     for (int j = 0; j < R.slot_count; j++) round_terms += S.slots[R.slot_begin + j].tn;
-    const bool inline_stage = round_terms <= kInlineTerms && R.slot_count <= kInlineSlots;
+    return round_terms <= kInlineTerms && R.slot_count <= kInlineSlots;
+}
+
+// The slot sums of a round's group exponentials for the tile (into ST) and
+// its tile-constant sums (into CST), without barriers.
+void emit_slot_sums(std::ostringstream &o, const Schedule &S, const DevPass &P, const DevRound &R, int NT) {
+    const bool inline_stage = round_inline_stage(S, R);
     if (P.term_cache && !inline_stage) {
         o << "      stage_slots(xo, kp.slots, " << R.slot_begin << ", " << R.slot_count
           << ", TCM, TCQ, " << P.term_begin << ", ST, tid, NT);\n";
@@ -237,6 +239,16 @@ void emit_round_staging(std::ostringstream &o, const Schedule &S, const DevPass 
         if (R.cst_count[cc] > 0)
             o << "      if (warp == " << (cc % (NT / 32)) << ") { const uint64_t v = warp_const_sum(xo, kp.cst_mo, kp.cst_q, "
               << R.cst_begin[cc] << ", " << R.cst_count[cc] << ", lane); if (lane == 0) CST[" << cc << "] = v; }\n";
+}
+
+// Staging of a round's group exponentials for the tile (slot sums, tile
+// constants, class totals), with the barriers around it.  Complex64 passes
+// bias the class totals by 2^31 (rounding to Q0.32 turns), complex128 passes
+// keep Q0.64.
+void emit_round_staging(std::ostringstream &o, const Schedule &S, const DevPass &P, const DevRound &R, int NT,
+                        bool dbl_state) {
+    const bool inline_stage = round_inline_stage(S, R);
+    emit_slot_sums(o, S, P, R, NT);
     o << "      __syncthreads();\n";
     // class totals, one thread each, spread over the warps
     if (!inline_stage)
@@ -256,6 +268,99 @@ void emit_round_staging(std::ostringstream &o, const Schedule &S, const DevPass 
         }
     }
     o << "      __syncthreads();\n";
+}
+
+// The round of a pass whose staging moves into the round before it: the
+// pass's only round with group exponentials, if its staging is straight-line
+// code.  Its slot sums are then formed while the previous round runs (for
+// the first round: in the last round of the previous tile, and before the
+// loop for the block's first tile), the barrier that opens the round orders
+// them, and each thread forms its class totals itself (emit_class_sums_full),
+// so that the round needs no barriers of its own for the staging.  A pass of
+// one round keeps its staging in place.  -1 if none.
+int hoisted_stage_round(const Schedule &S, const DevPass &P) {
+    int found = -1, count = 0;
+    for (int r = 0; r < P.n_rounds; r++)
+        if (S.rounds[P.round_begin + r].n_diag > 0) {
+            found = r;
+            count++;
+        }
+    if (count != 1 || P.n_rounds < 2) return -1;
+    return round_inline_stage(S, S.rounds[P.round_begin + found]) ? found : -1;
+}
+
+// The round in which the hoisted staging of round h is emitted: the round
+// before it, or the pass's last round (for the next tile) when h = 0.
+int staging_round(const DevPass &P, int h) { return h > 0 ? h - 1 : P.n_rounds - 1; }
+
+// Slot sums of the hoisted round h, emitted in round r = staging_round(h):
+// for this tile, or (h = 0) for the block's next tile.
+void emit_hoisted_slot_sums(std::ostringstream &o, const Schedule &S, const DevPass &P, int h, int NT) {
+    const DevRound &H = S.rounds[P.round_begin + h];
+    if (h > 0) {
+        emit_slot_sums(o, S, P, H, NT);
+        return;
+    }
+    o << "      if (tile + gridDim.x < ntiles) {\n        const uint64_t xo = deposit(tile + gridDim.x);\n";
+    emit_slot_sums(o, S, P, H, NT);
+    o << "      }\n";
+}
+
+// Whether round r (r >= 1) of a pass may open with a warp barrier instead of
+// a block barrier: it holds the same tile positions on the warp index as
+// round r - 1 (so every amplitude a warp reads from the exchange was written
+// by that warp), round r - 1 wrote the exchange without a permutation, and
+// round r reads nothing that other warps staged (its own staging, or the
+// slot sums hoisted into round r - 1).
+bool warp_local_round(const Schedule &S, const DevPass &P, int r, int hoist) {
+    if (r < 1) return false;
+    const DevRound &A = S.rounds[P.round_begin + r - 1], &B = S.rounds[P.round_begin + r];
+    if (A.perm >= 0 || B.n_diag > 0 || r == hoist) return false;
+    if (hoist >= 0 && staging_round(P, hoist) == r - 1) return false;
+    const int nw = S.K - kRegBits - kLaneBits;
+    uint32_t wa = 0, wb = 0;
+    for (int i = 0; i < nw; i++) {
+        wa |= 1u << A.warp_pos[i];
+        wb |= 1u << B.warp_pos[i];
+    }
+    return wa == wb;
+}
+
+// Dynamic shared memory of a generated pass: the interpreter's layout
+// (exchange buffer, prefetch buffer, staging, term cache) plus a second
+// prefetch buffer when it fits, so that the next tile's prefetch goes to the
+// other buffer right after the load, with no barrier in between.
+size_t jit_pass_smem(const Schedule &S, const DevPass &P, size_t amp, int K, bool *two) {
+    const size_t base = pass_smem_bytes(P, amp, K);
+    const bool t = S.prefetch > 1 && base + (amp << K) <= kTileSmemLimit;
+    if (two) *two = t;
+    return t ? base + (amp << K) : base;
+}
+
+// Class sums G[u] of a group exponential formed by the thread from the
+// staged slots alone: the bias, the class's slot constant over the fixed
+// positions, the tile constant (class 0), and each other slot of the class
+// with the sign of its parity with lf.
+void emit_class_sums_full(std::ostringstream &o, const Schedule &S, const DevRound &R, const DevDiag &d,
+                          uint64_t bias) {
+    for (int u = 0; u < 16; u++) {
+        if (!diag_class_used(d, u)) {
+            o << "        G[" << u << "] = 0ull;\n";
+            continue;
+        }
+        o << "        { uint64_t o0 = " << hex64(bias) << ", o1 = 0ull;\n";
+        if (d.zs[u] >= 0) o << "          o1 += ST[" << d.zs[u] << "].q;\n";
+        if (u == 0 && d.cst >= 0) o << "          o1 += CST[" << d.cst << "];\n";
+        for (int j = d.off[u]; j < d.off[u + 1]; j++) {
+            const uint32_t ml = S.slots[R.slot_begin + j].ml;
+            const char *acc = ((j - d.off[u]) & 1) ? "o1" : "o0";
+            o << "          { const uint64_t q = ST[" << j << "].q; " << acc << " += ";
+            if ((ml & (ml - 1)) == 0) o << "(lf & " << hex32(ml) << ")";
+            else o << "(__popc(lf & " << hex32(ml) << ") & 1)";
+            o << " ? 0ull - q : q; }\n";
+        }
+        o << "          G[" << u << "] = o0 + o1; }\n";
+    }
 }
 
 // Class sums G[u] of a group exponential for the thread (fixed positions lf):
@@ -306,13 +411,13 @@ void emit_io_prologue(std::ostringstream &o, const DevPass &P, int K, int NT, in
       << "  auto deposit = [&](long long t) -> uint64_t {\n"
       << "    return OUTT[0][t & 255] | OUTT[1][(t >> 8) & 255] | OUTT[2][(t >> 16) & 255] | OUTT[3][(t >> 24) & 255];\n"
       << "  };\n"
-      << "  auto prefetch = [&](long long t) {\n    const uint64_t xo = deposit(t) | sp_tid;\n";
+      << "  auto prefetch = [&](long long t, A *buf) {\n    const uint64_t xo = deposit(t) | sp_tid;\n";
     for (int k = 0; k < NCOPY; k++) {
         const uint64_t lk = (uint64_t)k * NT * E;
         uint64_t off = 0;
         for (int j = 0; j < K; j++)
             if ((lk >> j) & 1) off |= gbit(j);
-        o << "    cp_async16(Pf + (tid * E + " << lk << "), psi + (xo | " << hex64(off) << "));\n";
+        o << "    cp_async16(buf + (tid * E + " << lk << "), psi + (xo | " << hex64(off) << "));\n";
     }
     o << "    cp_async_commit();\n  };\n";
 }
@@ -335,6 +440,9 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     }
     const bool table_scaled = P.scale_in_diag && n_diag == 1;
     const double table_scale = table_scaled ? P.scale : 1.0;
+    const int hoist = hoisted_stage_round(S, P);
+    bool two = false;
+    jit_pass_smem(S, P, dbl_state ? 16 : 8, K, &two);
     // Complex128 passes run in fixed point (fx): each round ends with an
     // arithmetic shift that applies the 1/2 of each pair of its Hadamards
     // (a lone 1/sqrt(2) is carried to the next round); one left at the end of
@@ -364,8 +472,8 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
       << "  constexpr int K = " << K << ", NT = " << NT << ", E = " << E << ";\n"
       << "  extern __shared__ __align__(16) unsigned char smraw[];\n"
       << "  A *X = reinterpret_cast<A *>(smraw);\n"
-      << "  A *Pf = X + (1 << K);\n"
-      << "  StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf + (1 << K));\n"
+      << "  A *Pf0 = X + (1 << K), *Pf1 = Pf0 + " << (two ? "(1 << K)" : "0") << ";\n"
+      << "  StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf0 + " << (two ? 2 : 1) << " * (1 << K));\n"
       << "  uint64_t *TQ = reinterpret_cast<uint64_t *>(ST + " << (P.max_stage > 0 ? P.max_stage : 1) << ");\n"
       << "  (void)ST; (void)TQ;\n";
     if (P.term_cache)
@@ -410,17 +518,23 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     o << "  auto swz = [](uint32_t v) -> uint32_t {\n    return 0u";
     for (int p = 0; p < K; p++) o << " ^ (((v >> " << p << ") & 1u) * " << hex32((uint32_t)swc(p)) << ")";
     o << ";\n  };\n  (void)swz;\n";
-    o << "  long long tile = blockIdx.x;\n  if (tile < ntiles) prefetch(tile);\n"
-      << "  for (; tile < ntiles; tile += gridDim.x) {\n"
-      << "    const uint64_t xo = deposit(tile);\n";
+    o << "  long long tile = blockIdx.x;\n  int par = 0;\n  (void)Pf1;\n  if (tile < ntiles) prefetch(tile, Pf0);\n";
+    if (hoist == 0) {
+        o << "  if (tile < ntiles) {\n    const uint64_t xo = deposit(tile);\n";
+        emit_slot_sums(o, S, P, S.rounds[P.round_begin], NT);
+        o << "  }\n";
+    }
+    o << "  for (; tile < ntiles; tile += gridDim.x, par ^= " << (two ? 1 : 0) << ") {\n"
+      << "    const uint64_t xo = deposit(tile);\n"
+      << "    A *Pf = par ? Pf1 : Pf0;\n";
     if (fx) o << "    long long ar[16], ai[16];\n    uint32_t Sx = 0u;\n";
     else o << "    A a[16];\n";
     for (int r = 0; r < P.n_rounds; r++) {
         const DevRound &R = S.rounds[P.round_begin + r];
         o << "    { // round " << r << "\n";
         if (r == 0) o << "      cp_async_wait_all();\n";
-        o << "      __syncthreads();\n";
-        if (R.n_diag > 0) emit_round_staging(o, S, P, R, NT, dbl_state);
+        o << (warp_local_round(S, P, r, hoist) ? "      __syncwarp();\n" : "      __syncthreads();\n");
+        if (R.n_diag > 0 && r != hoist) emit_round_staging(o, S, P, R, NT, dbl_state);
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t sw = " << thread_expr(R, K, swc, false) << ";\n"
           << "      (void)lf; (void)sw;\n";
@@ -444,7 +558,8 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
               << "        for (int s = 0; s < 16; s++) { ar[s] = fx_from(d[s].x, Sx, " << fx_hr
               << "); ai[s] = fx_from(d[s].y, Sx, " << fx_hr << "); }\n"
               << "      }\n"
-              << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);\n";
+              << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
+              << ");\n";
         } else if (r == 0) {
             for (int s = 0; s < 16; s++) {
                 uint32_t l = 0;
@@ -452,8 +567,9 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                     if ((s >> i) & 1) l |= 1u << R.reg_pos[i];
                 o << "      a[" << s << "] = Pf[lf | " << hex32(l) << "];\n";
             }
-            o << "      __syncthreads();\n"
-              << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);\n";
+            if (!two) o << "      __syncthreads();\n";
+            o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
+              << ");\n";
         } else {
             for (int s = 0; s < 16; s++) {
                 uint32_t cs = 0;
@@ -466,6 +582,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                     o << "      a[" << s << "] = X[sw ^ " << hex32(cs) << "];\n";
             }
         }
+        if (hoist >= 0 && r == staging_round(P, hoist)) emit_hoisted_slot_sums(o, S, P, hoist, NT);
         int kph[16] = {0};   // fx: register s holds i^-kph[s] times its amplitude
         bool need_xf = (R.flags & 2) != 0;
         for (int oi = R.op_begin; oi < R.op_end; oi++)
@@ -491,7 +608,8 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                 const DevDiag &d = S.diags[op.arg];
                 const double sc = (op.pad && !table_scaled) ? P.scale : 1.0;
                 o << "      { uint64_t G[16];\n";
-                emit_class_sums(o, S, R, d);
+                if (r == hoist) emit_class_sums_full(o, S, R, d, dbl_state ? 0ull : (1ull << 31));
+                else emit_class_sums(o, S, R, d);
                 if (fx)
                     o << "        wht16(G);\n"
                       << "        #pragma unroll\n"
@@ -623,6 +741,9 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
     }
     const bool table_scaled = P.scale_in_diag && n_diag == 1;
     const double table_scale = table_scaled ? P.scale : 1.0;
+    const int hoist = hoisted_stage_round(S, P);
+    bool two = false;
+    jit_pass_smem(S, P, 8, K, &two);
     std::ostringstream o;
     o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << kernel_name(pi, false)
       << "(A *__restrict__ psi, sd::KParams kp) {\n"
@@ -630,9 +751,8 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
       << "  constexpr int K = " << K << ", NT = " << NT << ", E = " << E << ";\n"
       << "  extern __shared__ __align__(16) unsigned char smraw[];\n"
       << "  float4 *X4 = reinterpret_cast<float4 *>(smraw);\n"
-      << "  A *Pf = reinterpret_cast<A *>(smraw) + (1 << K);\n"
-      << "  const float4 *Pf4 = reinterpret_cast<const float4 *>(Pf);\n"
-      << "  StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf + (1 << K));\n"
+      << "  A *Pf0 = reinterpret_cast<A *>(smraw) + (1 << K), *Pf1 = Pf0 + " << (two ? "(1 << K)" : "0") << ";\n"
+      << "  StagedTerm *ST = reinterpret_cast<StagedTerm *>(Pf0 + " << (two ? 2 : 1) << " * (1 << K));\n"
       << "  uint64_t *TQ = reinterpret_cast<uint64_t *>(ST + " << (P.max_stage > 0 ? P.max_stage : 1) << ");\n"
       << "  (void)ST; (void)TQ;\n";
     if (P.term_cache)
@@ -660,9 +780,16 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
     o << "    }\n  }\n  __syncthreads();\n";
     emit_io_prologue(o, P, K, NT, E, n);
     o << "  const float2 M1 = make_float2(-1.f, -1.f);\n  (void)M1;\n"
-      << "  long long tile = blockIdx.x;\n  if (tile < ntiles) prefetch(tile);\n"
-      << "  for (; tile < ntiles; tile += gridDim.x) {\n"
+      << "  long long tile = blockIdx.x;\n  int par = 0;\n  (void)Pf1;\n  if (tile < ntiles) prefetch(tile, Pf0);\n";
+    if (hoist == 0) {
+        o << "  if (tile < ntiles) {\n    const uint64_t xo = deposit(tile);\n";
+        emit_slot_sums(o, S, P, S.rounds[P.round_begin], NT);
+        o << "  }\n";
+    }
+    o << "  for (; tile < ntiles; tile += gridDim.x, par ^= " << (two ? 1 : 0) << ") {\n"
       << "    const uint64_t xo = deposit(tile);\n"
+      << "    A *Pf = par ? Pf1 : Pf0;\n"
+      << "    const float4 *Pf4 = reinterpret_cast<const float4 *>(Pf);\n"
       << "    float2 R[8], I[8];\n";
     // register slot i (1..3) <-> bit i-1 of the pair index k
     auto slot_sum = [&](const DevRound &R, int k, const std::function<uint64_t(int)> &col) {
@@ -675,8 +802,8 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
         const DevRound &R = S.rounds[P.round_begin + r];
         o << "    { // round " << r << "\n";
         if (r == 0) o << "      cp_async_wait_all();\n";
-        o << "      __syncthreads();\n";
-        if (R.n_diag > 0) emit_round_staging(o, S, P, R, NT, false);
+        o << (warp_local_round(S, P, r, hoist) ? "      __syncwarp();\n" : "      __syncthreads();\n");
+        if (R.n_diag > 0 && r != hoist) emit_round_staging(o, S, P, R, NT, false);
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t swu = " << thread_expr(R, K, ucol, false) << ";\n"
           << "      (void)lf; (void)swu;\n";
@@ -684,14 +811,16 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
             for (int k = 0; k < 8; k++)
                 o << "      { const float4 v = Pf4[(lf | " << hex32((uint32_t)slot_sum(R, k, lcol))
                   << ") >> 1]; R[" << k << "] = make_float2(v.x, v.z); I[" << k << "] = make_float2(v.y, v.w); }\n";
-            o << "      __syncthreads();\n"
-              << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);\n";
+            if (!two) o << "      __syncthreads();\n";
+            o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
+              << ");\n";
         } else {
             for (int k = 0; k < 8; k++)
                 o << "      { const float4 v = X4[swu ^ " << hex32((uint32_t)slot_sum(R, k, ucol)) << "]; R[" << k
                   << "] = make_float2(v.x, v.y); I[" << k << "] = make_float2(v.z, v.w); }\n";
         }
         if (R.flags & 2) o << "      const uint64_t xf = xo | " << thread_expr(R, K, gbit, true) << ";\n";
+        if (hoist >= 0 && r == staging_round(P, hoist)) emit_hoisted_slot_sums(o, S, P, hoist, NT);
         int kph[8] = {0};
         for (int oi = R.op_begin; oi < R.op_end; oi++) {
             const DevOp &op = S.ops[oi];
@@ -764,7 +893,8 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
                 const DevDiag &d = S.diags[op.arg];
                 const double sc = (op.pad && !table_scaled) ? P.scale : 1.0;
                 o << "      { uint64_t G[16];\n";
-                emit_class_sums(o, S, R, d);
+                if (r == hoist) emit_class_sums_full(o, S, R, d, 1ull << 31);
+                else emit_class_sums(o, S, R, d);
                 o << "        uint32_t g[16];\n"
                   << "        #pragma unroll\n"
                   << "        for (int s = 0; s < 16; s++) g[s] = (uint32_t)(G[s] >> 32);\n"
@@ -999,7 +1129,7 @@ std::string jit_build(const Schedule &S, int n, bool dbl_state, JitProgram &out)
         const std::string name = kernel_name(p, dbl_state);
         if (g_drv.get_function(&f, mods[p / chunk], name.c_str()) != CUDA_SUCCESS) return "missing kernel " + name;
         const size_t amp = dbl_state ? 16 : 8;
-        const size_t smem = pass_smem_bytes(S.passes[p], amp, S.K);
+        const size_t smem = jit_pass_smem(S, S.passes[p], amp, S.K, nullptr);
         if (g_drv.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
             return "cuFuncSetAttribute failed";
         int occ = 0;

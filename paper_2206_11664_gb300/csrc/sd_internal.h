@@ -128,6 +128,9 @@ struct Schedule {
     // 1: tile position 0 (qubit 0) is register slot 0 in every round, so that
     // a thread's amplitudes pair up along it (packed two-amplitude layout).
     int pin0 = 0;
+    // Prefetch buffers of the passes compiled at run time (1 or 2; 2 only
+    // where the shared memory allows it).
+    int prefetch = 1;
     std::vector<DevPass> passes;
     std::vector<DevRound> rounds;
     std::vector<DevOp> ops;

@@ -46,9 +46,9 @@ def _rand_state(rng, n):
 
 
 def _check(sd, h, psi0, dt_, steps, order, dtype, skip_rule=-1, tile_bits=0, pauli=False, jit=0,
-           grouping=0, layout=0):
+           grouping=0, layout=0, prefetch=0):
     sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(skip_rule=skip_rule, tile_bits=tile_bits, jit=jit,
-                                                grouping=grouping, layout=layout)
+                                                grouping=grouping, layout=layout, prefetch=prefetch)
     groups = P.partition(h.x, h.z, grouping, h.c)
     ref = oracle.evolve(h, psi0, dt_, steps, order, groups)
     t = _dev(psi0, dtype)
@@ -482,6 +482,22 @@ def test_paired_layout(sd, order):
     _check(sd, h3, _rand_state(rng, 16), 0.02, 5, order, "c64", jit=1, layout=1)
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_two_prefetch_buffers(sd, dtype):
+    """Run-time passes with two prefetch buffers (no barrier between a tile's
+    load and the next tile's prefetch) against the oracle: Heisenberg blocks,
+    CNOT permutations and S/CZ layers, several tiles per block, both orders,
+    and the paired layout."""
+    h = heisenberg_lattice(4, 4)
+    _check(sd, h, basis_state(16, neel_index(4, 4)), 0.02, 6, 1, dtype, jit=1, prefetch=2)
+    rng = np.random.default_rng(69)
+    h2 = random_klocal(15, 50, rng, weights=(2, 3, 4))
+    _check(sd, h2, _rand_state(rng, 15), 0.05, 3, 2, dtype, skip_rule=0, jit=1, prefetch=2)
+    _check(sd, h2, _rand_state(rng, 15), 0.05, 2, 1, dtype, tile_bits=10, jit=1, prefetch=2)
+    if dtype == "c64":
+        _check(sd, h, basis_state(16, neel_index(4, 4)), 0.02, 6, 2, dtype, jit=1, layout=1, prefetch=2)
+
+
 def test_autotune_shape(sd, tmp_path):
     """The shape autotuner times tile sizes in both layouts of the run-time
     complex64 passes, keeps the fastest, stores it in a JSON cache that a
@@ -494,13 +510,14 @@ def test_autotune_shape(sd, tmp_path):
     res = sim.autotune_shape(sd.C64, 0.02, steps=4, order=1, kmin=12, kmax=13, cache=cache)
     assert not res["cached"]
     ms = {tuple(int(v) for v in k.split(",")): t for k, t in res["ms_per_step"].items()}
-    assert {lay for _, lay in ms} == {-1, 1} and all(t > 0 for t in ms.values())
-    best = (res["tile_bits"], res["layout"])
+    assert {lay for _, lay, _ in ms} == {-1, 1} and {pf for _, _, pf in ms} == {1, 2}
+    assert all(t > 0 for t in ms.values())
+    best = (res["tile_bits"], res["layout"], res["prefetch"])
     assert best in ms and ms[best] == min(ms.values())
     assert sim.schedule_stats(sd.C64, 1)["tile_bits"] == res["tile_bits"]
     again = sd.Simulator(h.n, h.x, h.z, h.c).plan()
     res2 = again.autotune_shape(sd.C64, 0.02, steps=4, order=1, kmin=12, kmax=13, cache=cache)
-    assert res2["cached"] and (res2["tile_bits"], res2["layout"]) == best
+    assert res2["cached"] and (res2["tile_bits"], res2["layout"], res2["prefetch"]) == best
     assert again.schedule_stats(sd.C64, 1)["tile_bits"] == res["tile_bits"]
     rng = np.random.default_rng(68)
     psi0 = _rand_state(rng, h.n)
