@@ -218,15 +218,32 @@ void append_circuit(Circuit &a, const Circuit &b) {
 // Pass schedule of a canonicalised circuit on the tile path: the default
 // tile size, or smaller tiles when a pass's staged terms do not fit beside
 // the tile in shared memory.
+// Circuits up to this many ops are scheduled twice, with and without
+// deferring single-gate last rounds (schedule_circuit), and the schedule with
+// fewer passes, then fewer rounds, is kept.
+constexpr size_t kTailTrialOps = 20000;
+
 sd_status schedule_for(sd_ctx *ctx, const Circuit &circ, bool dbl, Schedule &S, bool pin0 = false) {
     int K = default_tile_bits(ctx, dbl);
     const int c = dbl ? 3 : 4;
+    auto need_of = [&](const Schedule &X) {
+        size_t need = 0;
+        for (auto &p : X.passes) need = std::max(need, pass_smem_bytes(p, dbl ? 16 : 8, K));
+        return need;
+    };
     for (;;) {
         std::string e = schedule_circuit(circ, ctx->n, K, c, S, pin0);
         if (!e.empty()) return fail(ctx, SD_EINTERNAL, "scheduler: " + e);
-        size_t need = 0;
-        for (auto &p : S.passes) need = std::max(need, pass_smem_bytes(p, dbl ? 16 : 8, K));
-        if (need <= kTileSmemLimit) return SD_OK;
+        if (need_of(S) <= kTileSmemLimit) {
+            if (circ.ops.size() <= kTailTrialOps) {
+                Schedule T;
+                if (schedule_circuit(circ, ctx->n, K, c, T, pin0, true).empty() && need_of(T) <= kTileSmemLimit &&
+                    (T.passes.size() < S.passes.size() ||
+                     (T.passes.size() == S.passes.size() && T.rounds.size() < S.rounds.size())))
+                    S = std::move(T);
+            }
+            return SD_OK;
+        }
         if (K <= kRegBits + kLaneBits)
             return fail(ctx, SD_EINVAL, "a commuting group has too many terms for one tile pass");
         K--;   // smaller tiles leave room to stage the group's terms

@@ -326,6 +326,17 @@ bool warp_local_round(const Schedule &S, const DevPass &P, int r, int hoist) {
     return wa == wb;
 }
 
+// The round after whose opening block barrier a pass with one prefetch
+// buffer issues the next tile's prefetch: the first round r >= 1 that opens
+// with a block barrier (every thread has read the buffer in round 0 by then).
+// 0 when there is none: the prefetch then follows a barrier of its own in
+// round 0.
+int prefetch_round(const Schedule &S, const DevPass &P, int hoist) {
+    for (int r = 1; r < P.n_rounds; r++)
+        if (!warp_local_round(S, P, r, hoist)) return r;
+    return 0;
+}
+
 // Dynamic shared memory of a generated pass: the interpreter's layout
 // (exchange buffer, prefetch buffer, staging, term cache) plus a second
 // prefetch buffer when it fits, so that the next tile's prefetch goes to the
@@ -443,6 +454,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     const int hoist = hoisted_stage_round(S, P);
     bool two = false;
     jit_pass_smem(S, P, dbl_state ? 16 : 8, K, &two);
+    const int pf_round = prefetch_round(S, P, hoist);
     // Complex128 passes run in fixed point (fx): each round ends with an
     // arithmetic shift that applies the 1/2 of each pair of its Hadamards
     // (a lone 1/sqrt(2) is carried to the next round); one left at the end of
@@ -534,6 +546,8 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         o << "    { // round " << r << "\n";
         if (r == 0) o << "      cp_async_wait_all();\n";
         o << (warp_local_round(S, P, r, hoist) ? "      __syncwarp();\n" : "      __syncthreads();\n");
+        if (!fx && !two && r > 0 && r == pf_round)
+            o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, Pf);\n";
         if (R.n_diag > 0 && r != hoist) emit_round_staging(o, S, P, R, NT, dbl_state);
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t sw = " << thread_expr(R, K, swc, false) << ";\n"
@@ -567,9 +581,11 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                     if ((s >> i) & 1) l |= 1u << R.reg_pos[i];
                 o << "      a[" << s << "] = Pf[lf | " << hex32(l) << "];\n";
             }
-            if (!two) o << "      __syncthreads();\n";
-            o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
-              << ");\n";
+            if (two || pf_round == 0) {
+                if (!two) o << "      __syncthreads();\n";
+                o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
+                  << ");\n";
+            }
         } else {
             for (int s = 0; s < 16; s++) {
                 uint32_t cs = 0;
@@ -744,6 +760,7 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
     const int hoist = hoisted_stage_round(S, P);
     bool two = false;
     jit_pass_smem(S, P, 8, K, &two);
+    const int pf_round = prefetch_round(S, P, hoist);
     std::ostringstream o;
     o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << kernel_name(pi, false)
       << "(A *__restrict__ psi, sd::KParams kp) {\n"
@@ -803,6 +820,8 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
         o << "    { // round " << r << "\n";
         if (r == 0) o << "      cp_async_wait_all();\n";
         o << (warp_local_round(S, P, r, hoist) ? "      __syncwarp();\n" : "      __syncthreads();\n");
+        if (!two && r > 0 && r == pf_round)
+            o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, Pf);\n";
         if (R.n_diag > 0 && r != hoist) emit_round_staging(o, S, P, R, NT, false);
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t swu = " << thread_expr(R, K, ucol, false) << ";\n"
@@ -811,9 +830,11 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
             for (int k = 0; k < 8; k++)
                 o << "      { const float4 v = Pf4[(lf | " << hex32((uint32_t)slot_sum(R, k, lcol))
                   << ") >> 1]; R[" << k << "] = make_float2(v.x, v.z); I[" << k << "] = make_float2(v.y, v.w); }\n";
-            if (!two) o << "      __syncthreads();\n";
-            o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
-              << ");\n";
+            if (two || pf_round == 0) {
+                if (!two) o << "      __syncthreads();\n";
+                o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
+                  << ");\n";
+            }
         } else {
             for (int k = 0; k < 8; k++)
                 o << "      { const float4 v = X4[swu ^ " << hex32((uint32_t)slot_sum(R, k, ucol)) << "]; R[" << k

@@ -366,7 +366,7 @@ void assign_layout(DevRound &R, int K, int c, bool global_io, bool pin0) {
 
 }  // namespace
 
-std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &S, bool pin0) {
+std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &S, bool pin0, bool tail_deferral) {
     S = Schedule{};
     S.K = K;
     S.c = c;
@@ -737,6 +737,26 @@ std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule 
             }
             bool useful = executed > 0 || is_load;
             if (!useful) break;
+            // A last round that would carry a single one-qubit gate, when another
+            // pass follows anyway and the previous round can store: leave that
+            // gate to the next pass instead of paying a round (an exchange and
+            // a block barrier per tile) for it.
+            if (tail_deferral && nr >= 2 && more_passes && executed == 1 && R.n_diag == 0 && perm_cnots.empty() &&
+                (int)S.ops.size() == R.op_begin + 1 &&
+                (S.ops.back().kind == D_HAD || S.ops.back().kind == D_MONO)) {
+                const DevRound &prev = S.rounds.back();
+                bool can_store = prev.perm < 0;
+                for (int i = pin0 ? 1 : 0; i < 4; i++) can_store &= prev.reg_pos[i] >= c;
+                if (can_store) {
+                    if (S.ops.back().kind == D_HAD) h_count--;
+                    S.ops.pop_back();
+                    for (int j = 0; j < N; j++)
+                        if (done[j] == round_id) done[j] = -1;
+                    first = 0;
+                    while (first < N && done[first] >= 0) first++;
+                    break;
+                }
+            }
             S.rounds.push_back(R);
             nr++;
             round_id++;

@@ -150,7 +150,8 @@ struct Schedule {
 // c = log2(128 bytes / amplitude size).  pin0: keep tile position 0 in
 // register slot 0 of every round (see Schedule::pin0).  Returns "" or an
 // error.
-std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &out, bool pin0 = false);
+std::string schedule_circuit(const Circuit &circ, int n, int K, int c, Schedule &out, bool pin0 = false,
+                             bool tail_deferral = false);
 
 // Swizzle column of tile position p (identity on the low c bits).
 uint32_t swizzle_col(int p, int c);

@@ -32,7 +32,8 @@
 // (the input then ends before the state, and nothing is executed).
 // The input is binary, in this order: int32 n, int64 m, int32 skip_rule,
 // int32 K, int32 c (plus 16 to pin tile position 0 to register slot 0, the
-// paired complex64 schedule), int32 order, int32 reps, int64 steps, float64 dt,
+// paired complex64 schedule; plus 32 to leave single-gate last rounds to the
+// next pass), int32 order, int32 reps, int64 steps, float64 dt,
 // uint64 x[m], uint64 z[m], float64 coeffs[m], complex128 psi[2^n]. The
 // output is complex128 psi[2^n].
 #include <cmath>
@@ -230,9 +231,9 @@ void bank_stats(const Schedule &S, BankStats &b) {
 
 // Schedules a circuit (one-qubit runs canonicalised first).  A paired
 // schedule must keep tile position 0 in register slot 0 of every round.
-bool schedule(Circuit circ, int n, int K, int c, bool pin0, Schedule &S) {
+bool schedule(Circuit circ, int n, int K, int c, bool pin0, bool tail, Schedule &S) {
     canonicalize_1q(circ, n);
-    const std::string e = schedule_circuit(circ, n, K, c, S, pin0);
+    const std::string e = schedule_circuit(circ, n, K, c, S, pin0, tail);
     if (!e.empty()) std::fprintf(stderr, "schedule: %s\n", e.c_str());
     if (pin0)
         for (const DevRound &R : S.rounds)
@@ -256,7 +257,7 @@ int main(int argc, char **argv) {
               std::fread(&K, 4, 1, f) == 1 && std::fread(&c, 4, 1, f) == 1 && std::fread(&order, 4, 1, f) == 1 &&
               std::fread(&reps, 4, 1, f) == 1 && std::fread(&steps, 8, 1, f) == 1 && std::fread(&dt, 8, 1, f) == 1;
     ok = ok && reps >= 1;
-    const bool pin0 = (c >> 4) & 1;
+    const bool pin0 = (c >> 4) & 1, tail = (c >> 5) & 1;
     c &= 15;
     std::vector<uint64_t> x(m), z(m);
     std::vector<double> coef(m);
@@ -328,7 +329,7 @@ int main(int argc, char **argv) {
     BankStats banks;
     std::vector<Schedule> scheds(segs.size());
     for (size_t i = 0; i < segs.size(); i++) {
-        if (!schedule(segs[i].first, n, K, c, pin0, scheds[i])) return 1;
+        if (!schedule(segs[i].first, n, K, c, pin0, tail, scheds[i])) return 1;
         bank_stats(scheds[i], banks);
         Emulator em{n, scheds[i], psi};
         if (run)
@@ -342,7 +343,10 @@ int main(int argc, char **argv) {
         std::fwrite(psi.data(), 16, psi.size(), f);
         std::fclose(f);
     }
+    size_t rounds = 0;
+    for (size_t i = 0; i < segs.size(); i++) rounds += scheds[i].rounds.size() * (size_t)segs[i].second;
     std::printf("passes %zu\n", passes);
+    std::printf("rounds %zu\n", rounds);
     std::printf("banks %ld %ld %ld %ld\n", banks.rounds, banks.short_lanes, banks.perm_rounds, banks.short_perm);
     return 0;
 }

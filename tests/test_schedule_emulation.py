@@ -34,10 +34,10 @@ def emulator(tmp_path_factory):
     return exe
 
 
-def _run(exe, tmp_path, h, psi0, dt, steps, order, skip, K, c, reps=1, pin0=False):
+def _run(exe, tmp_path, h, psi0, dt, steps, order, skip, K, c, reps=1, pin0=False, tail=False):
     inp, out = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(inp, "wb") as f:
-        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c + 16 * pin0, order, reps, steps, dt))
+        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c + 16 * pin0 + 32 * tail, order, reps, steps, dt))
         f.write(np.ascontiguousarray(h.x, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.z, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.c, dtype=np.float64).tobytes())
@@ -66,12 +66,13 @@ def test_schedule_matches_oracle(emulator, tmp_path, case, skip):
     rng = np.random.default_rng(700 + 10 * case + skip)
     h = CASES[case][1](rng)
     groups = P.greedy_partition(h.x, h.z)
-    for order, K, c, pin0 in ((1, 9, 4, False), (2, 10, 3, False), (1, 11, 4, False), (2, 10, 4, True),
-                              (1, 11, 4, True)):
+    for order, K, c, pin0, tail in ((1, 9, 4, False, False), (2, 10, 3, False, False), (1, 11, 4, False, False),
+                                    (2, 10, 4, True, False), (1, 11, 4, True, False), (2, 9, 3, False, True),
+                                    (1, 10, 4, True, True)):
         if K > h.n:
             continue
         psi0 = _rand(rng, h.n)
-        got = _run(emulator, tmp_path, h, psi0, 0.05, 2, order, skip, K, c, pin0=pin0)
+        got = _run(emulator, tmp_path, h, psi0, 0.05, 2, order, skip, K, c, pin0=pin0, tail=tail)
         ref = oracle.evolve(h, psi0, 0.05, 2, order, groups)
         err = np.linalg.norm(got - ref)
         assert err < 1e-10, (CASES[case][0], skip, order, K, pin0, err)
@@ -88,27 +89,47 @@ def test_blocks_at_the_default_tile_sizes(emulator, tmp_path, order):
              jw_like(n=14, m=300, rng=rng)]
     for h in cases:
         groups = P.greedy_partition(h.x, h.z)
-        for K, c, pin0 in ((13, 4, False), (12, 3, False), (13, 4, True)):
+        for K, c, pin0, tail in ((13, 4, False, False), (12, 3, False, False), (13, 4, True, False),
+                                 (13, 4, False, True), (12, 3, False, True)):
             psi0 = _rand(rng, h.n)
-            got = _run(emulator, tmp_path, h, psi0, 0.03, 6, order, 2, K, c, reps=4, pin0=pin0)
+            got = _run(emulator, tmp_path, h, psi0, 0.03, 6, order, 2, K, c, reps=4, pin0=pin0, tail=tail)
             ref = oracle.evolve(h, psi0, 0.03, 6, order, groups)
             err = np.linalg.norm(got - ref)
             assert err < 1e-10, (h.n, h.m, order, K, pin0, err)
 
 
-def _schedule_only(exe, tmp_path, h, order, K, c, steps, reps, skip=2, pin0=False):
+def _schedule_only(exe, tmp_path, h, order, K, c, steps, reps, skip=2, pin0=False, tail=False, rounds=False):
     """Passes of a call and the bank statistics of its rounds, without a state."""
     inp = tmp_path / "sched.bin"
     with open(inp, "wb") as f:
-        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c + 16 * pin0, order, reps, steps, 0.02))
+        f.write(struct.pack("<iqiiiiiqd", h.n, h.m, skip, K, c + 16 * pin0 + 32 * tail, order, reps, steps, 0.02))
         f.write(np.ascontiguousarray(h.x, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.z, dtype=np.uint64).tobytes())
         f.write(np.ascontiguousarray(h.c, dtype=np.float64).tobytes())
     r = subprocess.run([exe, str(inp), "-"], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     lines = dict(line.split(None, 1) for line in r.stdout.strip().splitlines())
-    rounds, short_lanes, perm_rounds, short_perm = (int(v) for v in lines["banks"].split())
-    return int(lines["passes"]), rounds, short_lanes, perm_rounds, short_perm
+    nrounds, short_lanes, perm_rounds, short_perm = (int(v) for v in lines["banks"].split())
+    if rounds:
+        return int(lines["passes"]), int(lines["rounds"])
+    return int(lines["passes"]), nrounds, short_lanes, perm_rounds, short_perm
+
+
+def test_single_gate_rounds_left_to_the_next_pass(emulator, tmp_path):
+    """Leaving a single-gate last round to the next pass (the library schedules
+    both ways and keeps fewer passes, then fewer rounds): on the n = 32
+    benchmark call it keeps the pass count and removes about a fifth of the
+    rounds; on the n = 30 call it would add passes, so that schedule is not
+    the one kept there.  The results match the oracle (the emulation tests
+    above)."""
+    h32 = heisenberg_lattice(6, 6, drop_corners=True)
+    p0, r0 = _schedule_only(emulator, tmp_path, h32, 1, 13, 4, 20, 4, rounds=True)
+    p1, r1 = _schedule_only(emulator, tmp_path, h32, 1, 13, 4, 20, 4, tail=True, rounds=True)
+    assert p1 == p0 and r1 < 0.85 * r0
+    h30 = heisenberg_lattice(5, 6)
+    p0, _ = _schedule_only(emulator, tmp_path, h30, 1, 13, 4, 20, 4, rounds=True)
+    p1, _ = _schedule_only(emulator, tmp_path, h30, 1, 13, 4, 20, 4, tail=True, rounds=True)
+    assert p1 > p0
 
 
 def test_benchmark_rounds_are_free_of_bank_conflicts(emulator, tmp_path):
