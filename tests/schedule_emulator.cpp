@@ -33,7 +33,8 @@
 // The input is binary, in this order: int32 n, int64 m, int32 skip_rule,
 // int32 K, int32 c (plus 16 to pin tile position 0 to register slot 0, the
 // paired complex64 schedule; plus 32 to leave single-gate last rounds to the
-// next pass), int32 order, int32 reps, int64 steps, float64 dt,
+// next pass; plus 64 to rotate by the complex64 passes' Q0.32 angles),
+// int32 order, int32 reps, int64 steps, float64 dt,
 // uint64 x[m], uint64 z[m], float64 coeffs[m], complex128 psi[2^n]. The
 // output is complex128 psi[2^n].
 #include <cmath>
@@ -69,6 +70,12 @@ struct Emulator {
     int n;
     const Schedule &S;
     std::vector<cd> &psi;
+    // Complex64 angles: the class sums rounded to Q0.32 (bias 2^31, then the
+    // high word) and the Walsh-Hadamard transform in 32 bits, as the complex64
+    // passes form them; q32err is the largest distance (in turns, mod 1) from
+    // the exact Q0.64 angle.
+    bool q32 = false;
+    double q32err = 0.0;
 
     void run_pass(const DevPass &P) {
         const int K = S.K;
@@ -157,6 +164,7 @@ struct Emulator {
                 int s = 0;
                 for (int i = 0; i < 4; i++) s |= ((l >> R.reg_pos[i]) & 1) << i;
                 uint64_t angle = 0;
+                uint32_t angle32 = 0;
                 for (int u = 0; u < 16; u++) {
                     uint64_t G = (u == 0) ? cst : 0;
                     if (d.zs[u] >= 0) G += slot_sum(d.zs[u]);
@@ -165,9 +173,16 @@ struct Emulator {
                         G += (popc((uint64_t)l & S.slots[R.slot_begin + j].ml) & 1) ? (0 - Q) : Q;
                     }
                     angle += (popc((uint64_t)(s & u)) & 1) ? (0 - G) : G;
+                    const bool used = d.off[u + 1] > d.off[u] || d.zs[u] >= 0 || (u == 0 && d.cst >= 0);
+                    const uint32_t g = used ? (uint32_t)((G + (uint64_t(1) << 31)) >> 32) : 0u;
+                    angle32 += (popc((uint64_t)(s & u)) & 1) ? (0u - g) : g;
                 }
                 const double turns = (double)(int64_t)angle / 18446744073709551616.0;
-                a[l] *= std::polar(sc, -2.0 * M_PI * turns);
+                const double turns32 = (double)(int32_t)angle32 / 4294967296.0;
+                double dlt = turns32 - turns;
+                dlt -= std::nearbyint(dlt);
+                q32err = std::max(q32err, std::fabs(dlt));
+                a[l] *= std::polar(sc, -2.0 * M_PI * (q32 ? turns32 : turns));
             }
         }
     }
@@ -257,7 +272,7 @@ int main(int argc, char **argv) {
               std::fread(&K, 4, 1, f) == 1 && std::fread(&c, 4, 1, f) == 1 && std::fread(&order, 4, 1, f) == 1 &&
               std::fread(&reps, 4, 1, f) == 1 && std::fread(&steps, 8, 1, f) == 1 && std::fread(&dt, 8, 1, f) == 1;
     ok = ok && reps >= 1;
-    const bool pin0 = (c >> 4) & 1, tail = (c >> 5) & 1;
+    const bool pin0 = (c >> 4) & 1, tail = (c >> 5) & 1, q32 = (c >> 6) & 1;
     c &= 15;
     std::vector<uint64_t> x(m), z(m);
     std::vector<double> coef(m);
@@ -326,15 +341,18 @@ int main(int argc, char **argv) {
         segs.push_back({tail, 1});
     }
     size_t passes = 0;
+    double q32err = 0.0;
     BankStats banks;
     std::vector<Schedule> scheds(segs.size());
     for (size_t i = 0; i < segs.size(); i++) {
         if (!schedule(segs[i].first, n, K, c, pin0, tail, scheds[i])) return 1;
         bank_stats(scheds[i], banks);
         Emulator em{n, scheds[i], psi};
+        em.q32 = q32;
         if (run)
             for (int64_t r = 0; r < segs[i].second; r++)
                 for (const DevPass &P : scheds[i].passes) em.run_pass(P);
+        q32err = std::max(q32err, em.q32err);
         passes += scheds[i].passes.size() * (size_t)segs[i].second;
     }
     if (run) {
@@ -347,6 +365,7 @@ int main(int argc, char **argv) {
     for (size_t i = 0; i < segs.size(); i++) rounds += scheds[i].rounds.size() * (size_t)segs[i].second;
     std::printf("passes %zu\n", passes);
     std::printf("rounds %zu\n", rounds);
+    std::printf("q32err %.17g\n", q32err);
     std::printf("banks %ld %ld %ld %ld\n", banks.rounds, banks.short_lanes, banks.perm_rounds, banks.short_perm);
     return 0;
 }
