@@ -46,6 +46,8 @@ def parse():
                              "tfim_fc", "syk", "sweep"],
                     help="heisenberg30 is the benchmark line; the others measure the remaining "
                          "configurations and print their own line")
+    ap.add_argument("--grad-steps", dest="grad_steps", type=int, default=500,
+                    help="Trotter steps of the gradient workload's timed evaluation (500 in its configuration)")
     ap.add_argument("--tile-bits", dest="tile_bits", type=int, default=0,
                     help="tile size for the batch workload (0 = default)")
     ap.add_argument("--autotune", action="store_true",

@@ -145,12 +145,13 @@ def grad24(args):
     sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
     psi = torch.full((1 << 24,), 2.0 ** -12, dtype=torch.complex128, device="cuda")
     obs = z_average_observable(24)
+    steps = int(getattr(args, "grad_steps", 500))
     sim.grad(psi, 0.01, 5, obs, 1)                        # builds the programs
     t0 = time.perf_counter()
-    f, g = sim.grad(psi, 0.01, 500, obs, 1)
+    f, g = sim.grad(psi, 0.01, steps, obs, 1)
     t = time.perf_counter() - t0
-    _line("gradient evaluations/s (n=24, 200 coefficients, 500 steps)", 1 / t, "evaluations/s",
-          {"workload": "gradient_2local_n24", "n": 24, "terms": 200, "dt": 0.01, "steps": 500,
+    _line(f"gradient evaluations/s (n=24, 200 coefficients, {steps} steps)", 1 / t, "evaluations/s",
+          {"workload": "gradient_2local_n24", "n": 24, "terms": 200, "dt": 0.01, "steps": steps,
            "order": 1, "state": "complex128"}, seconds=t, value_f=f,
           grad_norm=float(np.linalg.norm(g)))
 

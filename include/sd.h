@@ -19,7 +19,9 @@
  *   - A Pauli string is a pair of n-bit masks (x, z): I (0,0), X (1,0),
  *     Z (0,1), Y (1,1).  Text strings: character q is qubit q.
  *   - A state is 2^n contiguous amplitudes in device memory, interleaved
- *     (re, im): float pairs for SD_C64, double pairs for SD_C128.
+ *     (re, im): float pairs for SD_C64, double pairs for SD_C128, starting
+ *     on a 16-byte boundary (other addresses give SD_EINVAL; the library's
+ *     copies move 16 bytes at a time).
  *
  * Errors.  Every call returns an sd_status; on failure nothing the caller
  * owns has been modified, except that a CUDA error (SD_ECUDA) or a timeout

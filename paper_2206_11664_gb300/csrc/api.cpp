@@ -509,6 +509,8 @@ sd_status check_state_args(sd_ctx *ctx, const void *state, sd_dtype dtype, int o
     if (!state) return fail(ctx, SD_EINVAL, "null state pointer");
     if (dtype != SD_C64 && dtype != SD_C128) return fail(ctx, SD_EINVAL, "dtype must be SD_C64 or SD_C128");
     if (order != 1 && order != 2) return fail(ctx, SD_EINVAL, "order must be 1 or 2");
+    // the passes move 16 bytes per copy (two complex64 or one complex128 amplitude)
+    if ((uintptr_t)state % 16 != 0) return fail(ctx, SD_EINVAL, "state must be 16-byte aligned");
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, state) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
         cudaGetLastError();
@@ -1389,9 +1391,17 @@ struct BatchEntry {
     double dt;
     int64_t steps;
     int order;
-    std::vector<int64_t> alone;   // instances run one by one (on chip, or mixed tile sizes)
+    std::vector<int64_t> alone;   // instances run like sd_evolve (on chip, large, or mixed tile sizes)
     std::vector<BatchGroup> groups;
+    // Streams on which the instances that run alone proceed side by side with
+    // each other and with the level launches, forked from and joined back to
+    // the caller's stream by events (also inside a stream capture).
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
 };
+// Side streams of a batch: at most this many.
+constexpr size_t kBatchSideStreams = 8;
 std::recursive_mutex g_batch_mu;
 // An instance with 2^8 or more tiles (a tile per SM at least) runs on its own.
 constexpr int kBatchAloneTileBits = 8;
@@ -1403,6 +1413,12 @@ void free_batch(BatchEntry &e) {
         cudaFree(g.d_inst);
         cudaFree(g.d_cta);
     }
+    for (cudaStream_t x : e.side) cudaStreamDestroy(x);
+    for (cudaEvent_t x : e.join) cudaEventDestroy(x);
+    if (e.fork) cudaEventDestroy(e.fork);
+    e.side.clear();
+    e.join.clear();
+    e.fork = nullptr;
 }
 
 void batch_purge(const sd_ctx *ctx) {
@@ -1545,6 +1561,24 @@ sd_status batch_entry(sd_ctx *const *ctxs, void *const *d_states, int64_t count,
             return fail(ctx, SD_ECUDA, std::string("batch descriptors: ") + cudaGetErrorString(ce));
         }
     }
+    // side streams for the instances that run alone, when there is anything
+    // to run beside them
+    const size_t nside = std::min(kBatchSideStreams, e.alone.size());
+    if (nside > 1 || (nside == 1 && !e.groups.empty())) {
+        cudaError_t ce = cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming);
+        for (size_t k = 0; k < nside && ce == cudaSuccess; k++) {
+            cudaStream_t x = nullptr;
+            cudaEvent_t ev = nullptr;
+            ce = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+            if (ce == cudaSuccess) e.side.push_back(x);
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (ce == cudaSuccess) e.join.push_back(ev);
+        }
+        if (ce != cudaSuccess) {
+            free_batch(e);
+            return fail(ctxs[0], SD_ECUDA, std::string("batch streams: ") + cudaGetErrorString(ce));
+        }
+    }
     g_batches.push_front(std::move(e));
     while (g_batches.size() > kBatchCache) {
         free_batch(g_batches.back());
@@ -1588,16 +1622,31 @@ sd_status sd_evolve_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t co
     std::lock_guard<std::recursive_mutex> lk(g_batch_mu);
     BatchEntry *e = nullptr;
     if ((s = batch_entry(ctxs, d_states, count, dtype, dt, steps, order, st, e)) != SD_OK) return s;
-    // Instances on the on-chip path (or with mixed tile sizes) run one by one;
-    // the others advance level by level, one launch per level for each tile size.
-    for (int64_t i : e->alone)
-        if ((s = evolve_impl(ctxs[i], d_states[i], dbl, dt, steps, order, st)) != SD_OK) return s;
+    // Instances on the on-chip path, large ones and those with mixed tile
+    // sizes run like sd_evolve, side by side on the batch's side streams; the
+    // others advance level by level on the caller's stream, one launch per
+    // level for each tile size.
+    sd_ctx *ctx = ctxs[0];   // where CUDA errors of the fork and join are reported
+    if (!e->side.empty()) {
+        CK(cudaEventRecord(e->fork, st));
+        for (cudaStream_t x : e->side) CK(cudaStreamWaitEvent(x, e->fork, 0));
+        for (size_t k = 0; k < e->alone.size(); k++) {
+            const int64_t i = e->alone[k];
+            if ((s = evolve_impl(ctxs[i], d_states[i], dbl, dt, steps, order, e->side[k % e->side.size()])) != SD_OK)
+                return s;
+        }
+        for (size_t k = 0; k < e->side.size(); k++) CK(cudaEventRecord(e->join[k], e->side[k]));
+    } else {
+        for (int64_t i : e->alone)
+            if ((s = evolve_impl(ctxs[i], d_states[i], dbl, dt, steps, order, st)) != SD_OK) return s;
+    }
     for (auto &g : e->groups)
         for (int64_t L = 0; L < g.levels; L++) {
             cudaError_t ce = launch_tile_pass_batch(dbl, g.K, g.d_inst, g.d_cta, g.ctas, g.smem, L, st);
             if (ce != cudaSuccess)
                 return fail(ctxs[0], SD_ECUDA, std::string("batch launch: ") + cudaGetErrorString(ce));
         }
+    for (cudaEvent_t x : e->join) CK(cudaStreamWaitEvent(st, x, 0));
     return SD_OK;
 }
 

@@ -447,6 +447,10 @@ def test_invalid_state_rejected(sd):
         sim.evolve(torch.zeros(1024, dtype=torch.complex64), 0.1, 1)
     with pytest.raises(sd.SDError):
         sim.evolve(torch.zeros(1024, dtype=torch.complex64, device="cuda"), 0.1, 1, order=3)
+    # a view that starts 8 bytes into an allocation is refused before any launch
+    big = torch.zeros(1025, dtype=torch.complex64, device="cuda")
+    with pytest.raises(sd.SDError, match="16-byte aligned"):
+        sim.evolve(big[1:], 0.1, 1)
 
 
 # ---------------------------------------------------------------- run-time specialised passes
