@@ -1331,6 +1331,8 @@ sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt, 
     const int G = (int)ctx->plan.groups.size();
     const int blocks = grad_blocks(ctx->n, ctx->num_sms);
     auto seq = step_sequence(G, order);
+    DevTables tabs;   // e^{2 pi i k/256} for the adjoint kernel's rotations
+    if ((s = device_tables(ctx, tabs)) != SD_OK) return s;
     // Reverse sweep over the group exponentials.  phi and lam stay in the
     // diagonal frame of the exponential at hand: C_g brings them into the
     // first one's, each change of group runs one merged program C_b C_a^dag,
@@ -1350,7 +1352,7 @@ sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt, 
                 if ((s = run_program(ctx, dbl, *tr, phi, 1, st)) != SD_OK) return s;
                 if ((s = run_program(ctx, dbl, *tr, lam, 1, st)) != SD_OK) return s;
             }
-            CK(launch_grad_diag(dbl, phi, lam, ctx->n, gg->g, gg->masks_f, gg->qinv, nullptr,
+            CK(launch_grad_diag(dbl, phi, lam, ctx->n, gg->g, gg->masks_f, gg->qinv, tabs.tw,
                                 ctx->d_partial, blocks, st));
             CK(launch_grad_finalize(ctx->d_partial, blocks, gg->g.m, gg->term_id, gg->factor,
                                     ctx->d_gacc, st));

@@ -710,11 +710,18 @@ __global__ void apply_observable_kernel(const typename VT<T>::A *__restrict__ ph
 
 // Gradient contribution at a group's diagonal point; 16 consecutive
 // amplitudes per thread (register bits = index bits 0..3).
+template <typename A> __device__ __forceinline__ A make_cplx(decltype(A::x) re, decltype(A::x) im) {
+    A a;
+    a.x = re;
+    a.y = im;
+    return a;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restrict__ mu, int n,
                  DevGrad g, const uint64_t *__restrict__ masks_f, const int64_t *__restrict__ qinv,
-                 double *__restrict__ partial) {
+                 const double2 *__restrict__ tw, double *__restrict__ partial) {
     using A = typename VT<T>::A;
     extern __shared__ double acc[];
     for (int j = threadIdx.x; j < g.m; j += blockDim.x) acc[j] = 0.0;
@@ -763,8 +770,15 @@ grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restr
         if (live) {
 #pragma unroll
             for (int s = 0; s < 16; s++) {
-                chi[xf + s] = rotate<T>(cv[s], G[s], (T)1);
-                mu[xf + s] = rotate<T>(mv[s], G[s], (T)1);
+                // one rotation factor e^{-2 pi i G} for both vectors; in double
+                // precision by the table and series (the FP64 rate of this GPU
+                // makes sincospi the kernel's largest cost)
+                T sn, cs;
+                if constexpr (sizeof(T) == 8) turns_cs_tw(G[s], tw, cs, sn);
+                else turns_sc(G[s], sn, cs);
+                A a = cv[s], b = mv[s];
+                chi[xf + s] = make_cplx<A>(a.x * cs + a.y * sn, a.y * cs - a.x * sn);
+                mu[xf + s] = make_cplx<A>(b.x * cs + b.y * sn, b.y * cs - b.x * sn);
             }
         }
     }
@@ -949,7 +963,7 @@ int grad_blocks(int n, int num_sms) {
 }
 
 cudaError_t launch_grad_diag(bool dbl, void *chi, void *mu, int n, const DevGrad &g,
-                             const uint64_t *masks_f, const int64_t *qinv, const int32_t *,
+                             const uint64_t *masks_f, const int64_t *qinv, const double2 *tw,
                              double *partial, int blocks, cudaStream_t st) {
     size_t smem = sizeof(double) * (size_t)(g.m > 0 ? g.m : 1);
     if (smem > 48 * 1024) {
@@ -962,11 +976,11 @@ cudaError_t launch_grad_diag(bool dbl, void *chi, void *mu, int n, const DevGrad
     if (dbl)
         grad_diag_kernel<double><<<blocks, 256, smem, st>>>(reinterpret_cast<double2 *>(chi),
                                                             reinterpret_cast<double2 *>(mu), n, g,
-                                                            masks_f, qinv, partial);
+                                                            masks_f, qinv, tw, partial);
     else
         grad_diag_kernel<float><<<blocks, 256, smem, st>>>(reinterpret_cast<float2 *>(chi),
                                                            reinterpret_cast<float2 *>(mu), n, g,
-                                                           masks_f, qinv, partial);
+                                                           masks_f, qinv, tw, partial);
     return cudaGetLastError();
 }
 
