@@ -193,6 +193,256 @@ void emit_mono_fx(std::ostringstream &o, int I, int PA, int XX, int *kph) {
     }
 }
 
+// ---------------------------------------------------- complex64 butterflies
+// A complex64 register slot may hold its amplitude v in one of eight
+// representations fixed at generation time: the stored pair p has
+// re v = sr p[sw] and im v = si p[1 - sw].  A butterfly (u, v) -> (u + i^PA v,
+// i^B (u - i^PA v)) whose two operands are stored with the same sw (after the
+// i^PA) is two packed f32x2 operations, u + D w and u - D w with a sign pair
+// D, and its second output simply takes the first operand's representation
+// times i^B.  Otherwise it is four scalar adds (signs and order are free in
+// scalar code), whose outputs may take any representation: the generator
+// picks those, and the output representations of a group exponential's
+// rotation, so that the following butterflies of the round pack.  Every slot
+// returns to the plain representation (sw = 0, sr = si = 1) before a store,
+// a quarter-turn layer and the end of the round.
+struct SlotRep {
+    int sw = 0, sr = 1, si = 1;
+};
+
+bool rep_plain(const SlotRep &r) { return r.sw == 0 && r.sr == 1 && r.si == 1; }
+
+// the representation of i^k v, stored in the same pair as v
+SlotRep rep_mul_i(SlotRep r, int k) {
+    for (k &= 3; k > 0; k--) r = SlotRep{1 - r.sw, -r.si, r.sr};
+    return r;
+}
+
+// A true component as a signed stored component: sign and index (0: .x, 1: .y).
+struct Comp {
+    int sign, idx;
+};
+Comp comp_re(const SlotRep &r) { return Comp{r.sr, r.sw}; }
+Comp comp_im(const SlotRep &r) { return Comp{r.si, 1 - r.sw}; }
+
+// sa a + sb b as one add with operand signs
+std::string signed_sum(int sa, const std::string &a, int sb, const std::string &b) {
+    if (sa > 0) return a + (sb > 0 ? " + " : " - ") + b;
+    if (sb > 0) return b + " - " + a;
+    return "-" + a + " - " + b;
+}
+
+struct C64Rounds {
+    SlotRep rep[16];
+
+    void reset() {
+        for (auto &r : rep) r = SlotRep{};
+    }
+    bool all_plain() const {
+        for (auto &r : rep)
+            if (!rep_plain(r)) return false;
+        return true;
+    }
+    // instructions that bring every slot back to the plain representation
+    int fixup_cost() const {
+        int c = 0;
+        for (auto &r : rep) c += rep_plain(r) ? 0 : (r.sw ? 2 : 1);
+        return c;
+    }
+    static bool packable(const SlotRep *rp, int I, int PA) {
+        for (int s = 0; s < 16; s++) {
+            if ((s >> I) & 1) continue;
+            if (rp[s].sw != rep_mul_i(rp[s | (1 << I)], PA).sw) return false;
+        }
+        return true;
+    }
+    // Representations that a scalar butterfly or a rotation at op k leaves:
+    // sw = parity of (s & L), signs +, for the L whose representations let
+    // the most following butterflies of the round pack.
+    static void target(const Schedule &S, const DevRound &R, int k, SlotRep *out) {
+        int best_L = 0, best = -1;
+        for (int L = 0; L < 16; L++) {
+            SlotRep rp[16];
+            for (int s = 0; s < 16; s++) rp[s] = SlotRep{__builtin_popcount(s & L) & 1, 1, 1};
+            int packed = 0;
+            for (int oi = k + 1; oi < R.op_end; oi++) {
+                const DevOp &op = S.ops[oi];
+                if (op.kind == D_PHASE || op.kind == D_DIAG) break;
+                const int I = op.slot;
+                if (op.kind == D_MONO) {
+                    for (int s = 0; s < 16; s++) {
+                        if ((s >> I) & 1) continue;
+                        const int t = s | (1 << I);
+                        rp[t] = rep_mul_i(rp[t], c1_a(op.arg));
+                        if (c1_x(op.arg)) std::swap(rp[s], rp[t]);
+                    }
+                    continue;
+                }
+                if (!packable(rp, I, c1_a(op.arg))) break;
+                packed++;
+                for (int s = 0; s < 16; s++)
+                    if (!((s >> I) & 1)) rp[s | (1 << I)] = rep_mul_i(rp[s], c1_b(op.arg));
+            }
+            if (packed > best || (packed == best && __builtin_popcount(L) < __builtin_popcount(best_L))) {
+                best = packed;
+                best_L = L;
+            }
+        }
+        for (int s = 0; s < 16; s++) out[s] = SlotRep{__builtin_popcount(s & best_L) & 1, 1, 1};
+    }
+    // whether op k is the round's last butterfly or rotation before the next
+    // quarter-turn layer or the round's end
+    static bool last_before_plain(const Schedule &S, const DevRound &R, int k) {
+        for (int oi = k + 1; oi < R.op_end; oi++) {
+            const int kind = S.ops[oi].kind;
+            if (kind == D_PHASE) return true;
+            if (kind == D_HAD || kind == D_DIAG) return false;
+        }
+        return true;
+    }
+    // reps after the ops k+1.. up to the next quarter-turn layer (monos only
+    // when op k is the last butterfly)
+    void after_monos(const Schedule &S, const DevRound &R, int k, SlotRep *rp) const {
+        for (int oi = k + 1; oi < R.op_end; oi++) {
+            const DevOp &op = S.ops[oi];
+            if (op.kind != D_MONO) break;
+            for (int s = 0; s < 16; s++) {
+                if ((s >> op.slot) & 1) continue;
+                const int t = s | (1 << op.slot);
+                rp[t] = rep_mul_i(rp[t], c1_a(op.arg));
+                if (c1_x(op.arg)) std::swap(rp[s], rp[t]);
+            }
+        }
+    }
+
+    void had(std::ostringstream &o, const Schedule &S, const DevRound &R, int k, bool free_fixup) {
+        const DevOp &op = S.ops[k];
+        const int I = op.slot, PA = c1_a(op.arg), B = c1_b(op.arg);
+        bool pack = packable(rep, I, PA);
+        const bool last = last_before_plain(S, R, k);
+        for (int oi = k + 1; oi < R.op_end; oi++)   // a quarter-turn layer comes before the store
+            if (S.ops[oi].kind == D_PHASE) free_fixup = false;
+        SlotRep out[16];
+        if (pack && last && !free_fixup) {
+            // packed, then back to plain, against scalar with plain outputs
+            SlotRep rp[16];
+            for (int s = 0; s < 16; s++) rp[s] = rep[s];
+            for (int s = 0; s < 16; s++)
+                if (!((s >> I) & 1)) rp[s | (1 << I)] = rep_mul_i(rp[s], B);
+            after_monos(S, R, k, rp);
+            int fix = 0;
+            for (auto &r : rp) fix += rep_plain(r) ? 0 : (r.sw ? 2 : 1);
+            pack = 16 + fix <= 32;
+        }
+        if (!pack) {
+            if (last) {
+                for (auto &r : out) r = SlotRep{};
+            } else {
+                target(S, R, k, out);
+            }
+        }
+        for (int s = 0; s < 16; s++) {
+            if ((s >> I) & 1) continue;
+            const int t = s | (1 << I);
+            const SlotRep Rs = rep[s], Rw = rep_mul_i(rep[t], PA);
+            if (pack) {
+                float d[2];
+                d[Rs.sw] = (float)(Rs.sr * Rw.sr);
+                d[1 - Rs.sw] = (float)(Rs.si * Rw.si);
+                auto add = [&](float e0, float e1) -> std::string {
+                    if (e0 > 0 && e1 > 0) return "__fadd2_rn(u, v)";
+                    return std::string("__ffma2_rn(v, make_float2(") + (e0 > 0 ? "1.f" : "-1.f") + ", " +
+                           (e1 > 0 ? "1.f" : "-1.f") + "), u)";
+                };
+                o << "      { const A u = a[" << s << "], v = a[" << t << "]; a[" << s << "] = " << add(d[0], d[1])
+                  << "; a[" << t << "] = " << add(-d[0], -d[1]) << "; }\n";
+                rep[t] = rep_mul_i(Rs, B);
+            } else {
+                // true parts of u, w = i^PA v and the outputs, as signed stored parts
+                static const char *sn[2] = {"s0", "s1"}, *tn[2] = {"t0", "t1"};
+                const Comp ur = comp_re(Rs), ui = comp_im(Rs), wr = comp_re(Rw), wi = comp_im(Rw);
+                // out1 = u + w; dif = u - w; out2 = i^B dif
+                struct Sum {
+                    int sa, ia, sb, ib;   // sa s[ia] + sb t[ib]
+                };
+                Sum o1r{ur.sign, ur.idx, wr.sign, wr.idx}, o1i{ui.sign, ui.idx, wi.sign, wi.idx};
+                Sum dr{ur.sign, ur.idx, -wr.sign, wr.idx}, di{ui.sign, ui.idx, -wi.sign, wi.idx};
+                for (int b = 0; b < (B & 3); b++) {   // i (re + i im) = -im + i re
+                    const Sum nr{-di.sa, di.ia, -di.sb, di.ib};
+                    di = dr;
+                    dr = nr;
+                }
+                auto store = [&](int slot, const SlotRep &ro, const Sum &re, const Sum &im) {
+                    // p[sw] = sr re, p[1 - sw] = si im
+                    const Sum c0 = ro.sw ? im : re, c1 = ro.sw ? re : im;
+                    const int f0 = ro.sw ? ro.si : ro.sr, f1 = ro.sw ? ro.sr : ro.si;
+                    o << " a[" << slot << "].x = " << signed_sum(f0 * c0.sa, sn[c0.ia], f0 * c0.sb, tn[c0.ib])
+                      << "; a[" << slot << "].y = " << signed_sum(f1 * c1.sa, sn[c1.ia], f1 * c1.sb, tn[c1.ib])
+                      << ";";
+                };
+                o << "      { const float s0 = a[" << s << "].x, s1 = a[" << s << "].y, t0 = a[" << t
+                  << "].x, t1 = a[" << t << "].y;";
+                store(s, out[s], o1r, o1i);
+                store(t, out[t], dr, di);
+                o << " }\n";
+            }
+        }
+        if (!pack)
+            for (int s = 0; s < 16; s++) rep[s] = out[s];
+    }
+
+    void mono(std::ostringstream &o, const DevOp &op) {
+        const int I = op.slot;
+        for (int s = 0; s < 16; s++) {
+            if ((s >> I) & 1) continue;
+            const int t = s | (1 << I);
+            rep[t] = rep_mul_i(rep[t], c1_a(op.arg));
+            if (c1_x(op.arg)) {
+                o << "      { const A w = a[" << s << "]; a[" << s << "] = a[" << t << "]; a[" << t << "] = w; }\n";
+                std::swap(rep[s], rep[t]);
+            }
+        }
+    }
+
+    // back to the plain representation
+    void plain(std::ostringstream &o) {
+        for (int s = 0; s < 16; s++) {
+            const SlotRep r = rep[s];
+            if (rep_plain(r)) continue;
+            if (r.sw == 0)
+                o << "      a[" << s << "] = __fmul2_rn(a[" << s << "], make_float2(" << (r.sr > 0 ? "1.f" : "-1.f")
+                  << ", " << (r.si > 0 ? "1.f" : "-1.f") << "));\n";
+            else
+                o << "      a[" << s << "] = make_float2(" << (r.sr > 0 ? "" : "-") << "a[" << s << "].y, "
+                  << (r.si > 0 ? "" : "-") << "a[" << s << "].x);\n";
+            rep[s] = SlotRep{};
+        }
+    }
+
+    // The group exponential's rotation of every slot, from its current
+    // representation to the ones the following butterflies want.
+    void rotate(std::ostringstream &o, const Schedule &S, const DevRound &R, int k, double sc) {
+        SlotRep out[16];
+        if (last_before_plain(S, R, k)) {
+            for (auto &r : out) r = SlotRep{};
+        } else {
+            target(S, R, k, out);
+        }
+        o << "        { uint32_t g[16];\n"
+          << "          #pragma unroll\n"
+          << "          for (int s = 0; s < 16; s++) g[s] = (uint32_t)(G[s] >> 32);\n"
+          << "          wht16(g);\n";
+        for (int s = 0; s < 16; s++) {
+            const SlotRep &ri = rep[s], &ro = out[s];
+            o << "          a[" << s << "] = rotate_tw32_rep<" << ri.sw << ", " << ri.sr << ", " << ri.si << ", "
+              << ro.sw << ", " << ro.sr << ", " << ro.si << ">(a[" << s << "], g[" << s << "], TW, (T)" << dbl(sc)
+              << ");\n";
+        }
+        o << "        }\n";
+        for (int s = 0; s < 16; s++) rep[s] = out[s];
+    }
+};
+
 // Limits of the straight-line code emitted for a round's group exponentials.
 constexpr int kInlineTerms = 384;   // terms staged per round
 constexpr int kInlineSlots = 192;   // slots per round / per exponential
@@ -600,6 +850,13 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
         }
         if (hoist >= 0 && r == staging_round(P, hoist)) emit_hoisted_slot_sums(o, S, P, hoist, NT);
         int kph[16] = {0};   // fx: register s holds i^-kph[s] times its amplitude
+        C64Rounds reps;      // complex64: the slots' representations
+        reps.reset();
+        // SD_C64_SCALAR=1 emits every butterfly as plain scalar code (the
+        // reference the CPU tests compare the packed code with)
+        const bool packed_bf = !fx && !getenv("SD_C64_SCALAR");
+        // the last round's store folds the representations into its scale
+        const bool store_folds = (R.flags & 2) && pass_scale != 1.0;
         bool need_xf = (R.flags & 2) != 0;
         for (int oi = R.op_begin; oi < R.op_end; oi++)
             need_xf |= S.ops[oi].kind == D_PHASE;
@@ -610,11 +867,16 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                 emit_had_fx(o, op.slot, c1_a(op.arg), c1_b(op.arg), kph);
             } else if (op.kind == D_MONO && fx) {
                 emit_mono_fx(o, op.slot, c1_a(op.arg), c1_x(op.arg), kph);
+            } else if (op.kind == D_HAD && packed_bf) {
+                reps.had(o, S, R, oi, store_folds);
+            } else if (op.kind == D_MONO && packed_bf) {
+                reps.mono(o, op);
             } else if (op.kind == D_HAD) {
                 o << "      had_fixed<" << op.slot << ", " << c1_a(op.arg) << ", " << c1_b(op.arg) << ">(a);\n";
             } else if (op.kind == D_MONO) {
                 o << "      mono_fixed<" << op.slot << ", " << c1_a(op.arg) << ", " << c1_x(op.arg) << ">(a);\n";
             } else if (op.kind == D_PHASE) {
+                if (packed_bf) reps.plain(o);
                 o << "      { const int gq[4] = {" << (int)P.tile_bits[R.reg_pos[0]] << ", "
                   << (int)P.tile_bits[R.reg_pos[1]] << ", " << (int)P.tile_bits[R.reg_pos[2]] << ", "
                   << (int)P.tile_bits[R.reg_pos[3]] << "};\n"
@@ -631,11 +893,15 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                       << "        #pragma unroll\n"
                       << "        for (int s = 0; s < 16; s++) fx_rotate(ar[s], ai[s], G[s], T1, T2);\n"
                       << "      }\n";
-                else
+                else if (packed_bf) {
+                    reps.rotate(o, S, R, oi, sc);
+                    o << "      }\n";
+                } else
                     o << "        diag_rotate(a, G, TW, (T)" << dbl(sc) << ");\n"
                       << "      }\n";
             }
         }
+        if (packed_bf && !store_folds) reps.plain(o);
         if (fx) {
             const int sh = fx_shift[r];
             if (sh > 0)
@@ -663,7 +929,17 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                 uint64_t g = 0;
                 for (int i = 0; i < 4; i++)
                     if ((s >> i) & 1) g |= gbit(R.reg_pos[i]);
-                if (pass_scale != 1.0)
+                if (pass_scale != 1.0 && packed_bf) {
+                    // the slot's representation folded into the scale
+                    const SlotRep &rp = reps.rep[s];
+                    const std::string fr = dbl(rp.sr * pass_scale), fi = dbl(rp.si * pass_scale);
+                    if (rp.sw == 0)
+                        o << "      psi[xf | " << hex64(g) << "] = __fmul2_rn(a[" << s << "], make_float2((T)" << fr
+                          << ", (T)" << fi << "));\n";
+                    else
+                        o << "      psi[xf | " << hex64(g) << "] = make_float2(a[" << s << "].y * (T)" << fr << ", a["
+                          << s << "].x * (T)" << fi << ");\n";
+                } else if (pass_scale != 1.0)
                     o << "      { A w = a[" << s << "]; w.x *= (T)" << dbl(pass_scale) << "; w.y *= (T)"
                       << dbl(pass_scale) << "; psi[xf | " << hex64(g) << "] = w; }\n";
                 else

@@ -151,6 +151,24 @@ __device__ __forceinline__ float2 rotate_tw32(float2 a, uint32_t t, const float2
     o.y = a.y * C - a.x * S;
     return o;
 }
+// rotate_tw32 for an amplitude held in one of the representations of the
+// complex64 passes' butterflies: the stored pair p has re = SRI p[SWI] and
+// im = SII p[1 - SWI] (signs +-1), and the result is stored the same way
+// with SWO, SRO, SIO.  The signs and the order fold into the arithmetic.
+template <int SWI, int SRI, int SII, int SWO, int SRO, int SIO>
+__device__ __forceinline__ float2 rotate_tw32_rep(float2 p, uint32_t t, const float2 *__restrict__ tw, float sc) {
+    const float2 v = make_float2((float)SRI * (SWI ? p.y : p.x), (float)SII * (SWI ? p.x : p.y));
+    const float2 r = rotate_tw32(v, t, tw, sc);
+    float2 q;
+    if (SWO) {
+        q.y = (float)SRO * r.x;
+        q.x = (float)SIO * r.y;
+    } else {
+        q.x = (float)SRO * r.x;
+        q.y = (float)SIO * r.y;
+    }
+    return q;
+}
 __device__ __forceinline__ double2 rotate_tw(double2 a, uint64_t t, const double2 *__restrict__ tw, double sc) {
     const double2 e = tw[t >> 56];
     const uint64_t r = (t << 8) >> 12;             // 52 bits below the table index

@@ -167,6 +167,33 @@ def test_large_diagonal_groups(sd, jit):
             _check(sd, h, _rand_state(rng, n), 0.05, 2, 1, dtype, jit=jit)
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_split_calls_resume(sd, order):
+    """The state is the checkpoint: evolving 3 steps, copying the state to the
+    host and back, then evolving 6 more gives the 9-step evolution (each call
+    opens and closes its own half steps in second order, and runs its own
+    block programs, so only the rounding differs), and both match the oracle."""
+    import torch
+    h = heisenberg_lattice(4, 5)                      # n = 20: run-time compiled passes
+    rng = np.random.default_rng(92 + order)
+    psi0 = _rand_state(rng, h.n)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    groups = P.greedy_partition(h.x, h.z)
+    ref = oracle.evolve(h, psi0, 0.02, 9, order, groups)
+    for dtype in ("c128", "c64"):
+        whole = _dev(psi0, dtype)
+        sim.evolve(whole, 0.02, 9, order)
+        part = _dev(psi0, dtype)
+        sim.evolve(part, 0.02, 3, order)
+        saved = part.cpu()                             # checkpoint on the host
+        part = saved.cuda()
+        sim.evolve(part, 0.02, 6, order)
+        diff = torch.linalg.vector_norm((whole - part).to(torch.complex128)).item()
+        assert diff <= TOL[dtype], (dtype, diff)
+        for t in (whole, part):
+            assert np.linalg.norm(_host(t) - ref) <= TOL[dtype]
+
+
 def test_trivial_calls(sd):
     """steps = 0 leaves the state alone; dt = 0 is the identity within the
     tolerance; a Hamiltonian of single-qubit X terms on the tile path."""
