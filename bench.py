@@ -50,6 +50,8 @@ def parse():
                     help="Trotter steps of the gradient workload's timed evaluation (500 in its configuration)")
     ap.add_argument("--tile-bits", dest="tile_bits", type=int, default=0,
                     help="tile size for the batch workload (0 = default)")
+    ap.add_argument("--prefetch", type=int, default=0, choices=[0, 1, 2],
+                    help="prefetch buffers of the passes compiled at run time (0 = the library's choice)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the tile size (K = 11..13) and, for complex64, the register layout by "
                          "timing them first (sd_autotune_shape)")
@@ -317,7 +319,7 @@ def main():
     dev = torch.device("cuda", local)
     h, neel, name = workload(args.qubits)
     n = h.n
-    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan(prefetch=args.prefetch)
     code = sd.C64 if args.state == "c64" else sd.C128
     cdt = torch.complex64 if args.state == "c64" else torch.complex128
     amp_bytes = 8 if args.state == "c64" else 16

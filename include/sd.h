@@ -100,11 +100,12 @@ typedef struct {
      * register round in some passes); 0 = default (plain, or what
      * sd_autotune_shape chose).  Complex128 passes ignore it. */
     int layout;
-    /* Tiles in flight in the passes compiled at run time: 1 = one prefetch
-     * buffer (the next tile is loaded after a barrier that follows the load
-     * of the current one); 2 = two buffers (no such barrier; 64 KB more
-     * shared memory, used only where it fits); 0 = default (1, or what
-     * sd_autotune_shape chose). */
+    /* Prefetch buffers of the passes compiled at run time: 1 = one (the
+     * next tile is loaded into it once every thread has read the current
+     * one); 2 = two (the next two tiles are in flight while a block works on
+     * a third; 64 KB more shared memory, used only where it fits); 0 =
+     * default (what sd_autotune_shape chose, else 1 for complex64 and 2 for
+     * complex128 states). */
     int prefetch;
     int reserved[2];
 } sd_plan_opts;

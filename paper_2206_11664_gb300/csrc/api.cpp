@@ -263,11 +263,12 @@ bool jit_wanted(const sd_ctx *ctx, bool allow_jit, int64_t passes) {
 }
 
 // Prefetch buffers of the run-time passes: sd_plan's choice, else the tuned
-// one, else one.
+// one, else one for complex64 (its passes gain nothing from a second) and two
+// for complex128 (whose slower passes do).
 int prefetch_buffers(const sd_ctx *ctx, bool dbl) {
     if (ctx->prefetch_opt > 0) return ctx->prefetch_opt;
     const int t = ctx->tuned_prefetch[dbl ? 1 : 0];
-    return t > 0 ? t : 1;
+    return t > 0 ? t : (dbl ? 2 : 1);
 }
 
 // With the paired layout, complex64 programs that will probably be compiled

@@ -588,9 +588,9 @@ int prefetch_round(const Schedule &S, const DevPass &P, int hoist) {
 }
 
 // Dynamic shared memory of a generated pass: the interpreter's layout
-// (exchange buffer, prefetch buffer, staging, term cache) plus a second
-// prefetch buffer when it fits, so that the next tile's prefetch goes to the
-// other buffer right after the load, with no barrier in between.
+// (exchange buffer, prefetch buffer, staging, term cache) plus, when asked
+// for and when it fits, a second prefetch buffer, so that two tiles are in
+// flight while the block works on a third.
 size_t jit_pass_smem(const Schedule &S, const DevPass &P, size_t amp, int K, bool *two) {
     const size_t base = pass_smem_bytes(P, amp, K);
     const bool t = S.prefetch > 1 && base + (amp << K) <= kTileSmemLimit;
@@ -704,6 +704,10 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     const int hoist = hoisted_stage_round(S, P);
     bool two = false;
     jit_pass_smem(S, P, dbl_state ? 16 : 8, K, &two);
+    // With two prefetch buffers the next two tiles are in flight: tile t's
+    // buffer, once every thread has read it, receives tile t + 2 grid.
+    const std::string pf_next = two ? "      if (tile + 2ll * gridDim.x < ntiles) prefetch(tile + 2ll * gridDim.x, Pf);\n"
+                                    : "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, Pf);\n";
     const int pf_round = prefetch_round(S, P, hoist);
     // Complex128 passes run in fixed point (fx): each round ends with an
     // arithmetic shift that applies the 1/2 of each pair of its Hadamards
@@ -781,6 +785,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     for (int p = 0; p < K; p++) o << " ^ (((v >> " << p << ") & 1u) * " << hex32((uint32_t)swc(p)) << ")";
     o << ";\n  };\n  (void)swz;\n";
     o << "  long long tile = blockIdx.x;\n  int par = 0;\n  (void)Pf1;\n  if (tile < ntiles) prefetch(tile, Pf0);\n";
+    if (two) o << "  if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, Pf1);\n";
     if (hoist == 0) {
         o << "  if (tile < ntiles) {\n    const uint64_t xo = deposit(tile);\n";
         emit_slot_sums(o, S, P, S.rounds[P.round_begin], NT);
@@ -794,10 +799,11 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
     for (int r = 0; r < P.n_rounds; r++) {
         const DevRound &R = S.rounds[P.round_begin + r];
         o << "    { // round " << r << "\n";
-        if (r == 0) o << "      cp_async_wait_all();\n";
+        if (r == 0)
+            o << (two ? "      if (tile + gridDim.x < ntiles) cp_async_wait_one(); else cp_async_wait_all();\n"
+                      : "      cp_async_wait_all();\n");
         o << (warp_local_round(S, P, r, hoist) ? "      __syncwarp();\n" : "      __syncthreads();\n");
-        if (!fx && !two && r > 0 && r == pf_round)
-            o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, Pf);\n";
+        if (!fx && r > 0 && r == pf_round) o << pf_next;
         if (R.n_diag > 0 && r != hoist) emit_round_staging(o, S, P, R, NT, dbl_state);
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t sw = " << thread_expr(R, K, swc, false) << ";\n"
@@ -822,8 +828,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
               << "        for (int s = 0; s < 16; s++) { ar[s] = fx_from(d[s].x, Sx, " << fx_hr
               << "); ai[s] = fx_from(d[s].y, Sx, " << fx_hr << "); }\n"
               << "      }\n"
-              << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
-              << ");\n";
+              << pf_next;
         } else if (r == 0) {
             for (int s = 0; s < 16; s++) {
                 uint32_t l = 0;
@@ -831,11 +836,7 @@ std::string gen_pass(const Schedule &S, int pi, int n, bool dbl_state) {
                     if ((s >> i) & 1) l |= 1u << R.reg_pos[i];
                 o << "      a[" << s << "] = Pf[lf | " << hex32(l) << "];\n";
             }
-            if (two || pf_round == 0) {
-                if (!two) o << "      __syncthreads();\n";
-                o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
-                  << ");\n";
-            }
+            if (pf_round == 0) o << "      __syncthreads();\n" << pf_next;
         } else {
             for (int s = 0; s < 16; s++) {
                 uint32_t cs = 0;
@@ -1036,6 +1037,8 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
     const int hoist = hoisted_stage_round(S, P);
     bool two = false;
     jit_pass_smem(S, P, 8, K, &two);
+    const std::string pf_next = two ? "      if (tile + 2ll * gridDim.x < ntiles) prefetch(tile + 2ll * gridDim.x, Pf);\n"
+                                    : "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, Pf);\n";
     const int pf_round = prefetch_round(S, P, hoist);
     std::ostringstream o;
     o << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << kernel_name(pi, false)
@@ -1074,6 +1077,7 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
     emit_io_prologue(o, P, K, NT, E, n);
     o << "  const float2 M1 = make_float2(-1.f, -1.f);\n  (void)M1;\n"
       << "  long long tile = blockIdx.x;\n  int par = 0;\n  (void)Pf1;\n  if (tile < ntiles) prefetch(tile, Pf0);\n";
+    if (two) o << "  if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, Pf1);\n";
     if (hoist == 0) {
         o << "  if (tile < ntiles) {\n    const uint64_t xo = deposit(tile);\n";
         emit_slot_sums(o, S, P, S.rounds[P.round_begin], NT);
@@ -1094,10 +1098,11 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
     for (int r = 0; r < P.n_rounds; r++) {
         const DevRound &R = S.rounds[P.round_begin + r];
         o << "    { // round " << r << "\n";
-        if (r == 0) o << "      cp_async_wait_all();\n";
+        if (r == 0)
+            o << (two ? "      if (tile + gridDim.x < ntiles) cp_async_wait_one(); else cp_async_wait_all();\n"
+                      : "      cp_async_wait_all();\n");
         o << (warp_local_round(S, P, r, hoist) ? "      __syncwarp();\n" : "      __syncthreads();\n");
-        if (!two && r > 0 && r == pf_round)
-            o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, Pf);\n";
+        if (r > 0 && r == pf_round) o << pf_next;
         if (R.n_diag > 0 && r != hoist) emit_round_staging(o, S, P, R, NT, false);
         o << "      const uint32_t lf = " << thread_expr(R, K, lcol, false) << ";\n"
           << "      const uint32_t swu = " << thread_expr(R, K, ucol, false) << ";\n"
@@ -1106,11 +1111,7 @@ std::string gen_pass_packed(const Schedule &S, int pi, int n) {
             for (int k = 0; k < 8; k++)
                 o << "      { const float4 v = Pf4[(lf | " << hex32((uint32_t)slot_sum(R, k, lcol))
                   << ") >> 1]; R[" << k << "] = make_float2(v.x, v.z); I[" << k << "] = make_float2(v.y, v.w); }\n";
-            if (two || pf_round == 0) {
-                if (!two) o << "      __syncthreads();\n";
-                o << "      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x, " << (two ? "par ? Pf0 : Pf1" : "Pf")
-                  << ");\n";
-            }
+            if (pf_round == 0) o << "      __syncthreads();\n" << pf_next;
         } else {
             for (int k = 0; k < 8; k++)
                 o << "      { const float4 v = X4[swu ^ " << hex32((uint32_t)slot_sum(R, k, ucol)) << "]; R[" << k

@@ -721,10 +721,14 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restrict__ mu, int n,
                  DevGrad g, const uint64_t *__restrict__ masks_f, const int64_t *__restrict__ qinv,
-                 const double2 *__restrict__ tw, double *__restrict__ partial) {
+                 const double2 *__restrict__ tw, double *__restrict__ partial, int per_thread) {
     using A = typename VT<T>::A;
+    // per_thread: acc[j * blockDim.x + tid] is thread tid's own sum for term
+    // j (one add per term and chunk, reduced once at the end); otherwise
+    // acc[j] takes each warp's shuffle-reduced sum
     extern __shared__ double acc[];
-    for (int j = threadIdx.x; j < g.m; j += blockDim.x) acc[j] = 0.0;
+    const int nacc = per_thread ? g.m * (int)blockDim.x : g.m;
+    for (int j = threadIdx.x; j < nacc; j += blockDim.x) acc[j] = 0.0;
     __syncthreads();
     const int64_t nchunks = ((int64_t)1 << n) >> 4;
     const int lane = threadIdx.x & 31;
@@ -752,8 +756,12 @@ grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restr
         for (int s = 0; s < 16; s++) {
             for (int j = g.off[s]; j < g.off[s + 1]; j++) {
                 double v = (popc64(xf & __ldg(masks_f + b + j)) & 1) ? -w[s] : w[s];
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if (lane == 0) atomicAdd(&acc[j], v);
+                if (per_thread) {
+                    acc[j * (int)blockDim.x + (int)threadIdx.x] += v;
+                } else {
+                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                    if (lane == 0) atomicAdd(&acc[j], v);
+                }
             }
         }
         uint64_t G[16];
@@ -783,7 +791,17 @@ grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restr
         }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < g.m; j += blockDim.x) partial[(int64_t)blockIdx.x * g.m + j] = acc[j];
+    if (per_thread) {
+        const int nw = (int)blockDim.x >> 5, wp = (int)threadIdx.x >> 5;
+        for (int j = wp; j < g.m; j += nw) {
+            double v = 0.0;
+            for (int t = lane; t < (int)blockDim.x; t += 32) v += acc[j * (int)blockDim.x + t];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) partial[(int64_t)blockIdx.x * g.m + j] = v;
+        }
+    } else {
+        for (int j = threadIdx.x; j < g.m; j += blockDim.x) partial[(int64_t)blockIdx.x * g.m + j] = acc[j];
+    }
 }
 
 
@@ -965,7 +983,10 @@ int grad_blocks(int n, int num_sms) {
 cudaError_t launch_grad_diag(bool dbl, void *chi, void *mu, int n, const DevGrad &g,
                              const uint64_t *masks_f, const int64_t *qinv, const double2 *tw,
                              double *partial, int blocks, cudaStream_t st) {
-    size_t smem = sizeof(double) * (size_t)(g.m > 0 ? g.m : 1);
+    // per-thread term sums while they fit beside nothing else in shared memory
+    constexpr int kThreads = 256;
+    const int per_thread = (size_t)g.m * kThreads * sizeof(double) <= 160 * 1024 ? 1 : 0;
+    size_t smem = sizeof(double) * (size_t)(g.m > 0 ? g.m : 1) * (per_thread ? kThreads : 1);
     if (smem > 48 * 1024) {
         cudaError_t e = dbl ? cudaFuncSetAttribute(grad_diag_kernel<double>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
@@ -974,13 +995,13 @@ cudaError_t launch_grad_diag(bool dbl, void *chi, void *mu, int n, const DevGrad
         if (e != cudaSuccess) return e;
     }
     if (dbl)
-        grad_diag_kernel<double><<<blocks, 256, smem, st>>>(reinterpret_cast<double2 *>(chi),
-                                                            reinterpret_cast<double2 *>(mu), n, g,
-                                                            masks_f, qinv, tw, partial);
+        grad_diag_kernel<double><<<blocks, kThreads, smem, st>>>(reinterpret_cast<double2 *>(chi),
+                                                                 reinterpret_cast<double2 *>(mu), n, g,
+                                                                 masks_f, qinv, tw, partial, per_thread);
     else
-        grad_diag_kernel<float><<<blocks, 256, smem, st>>>(reinterpret_cast<float2 *>(chi),
-                                                           reinterpret_cast<float2 *>(mu), n, g,
-                                                           masks_f, qinv, tw, partial);
+        grad_diag_kernel<float><<<blocks, kThreads, smem, st>>>(reinterpret_cast<float2 *>(chi),
+                                                                reinterpret_cast<float2 *>(mu), n, g,
+                                                                masks_f, qinv, tw, partial, per_thread);
     return cudaGetLastError();
 }
 

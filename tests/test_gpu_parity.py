@@ -16,6 +16,7 @@ from workloads import (from_strings, heisenberg_lattice, jw_like, neel_index, ra
                        tfim_chain, basis_state, plus_state, product_state, haar_product_factors,
                        tfim_fully_connected, syk_majorana,
                        gradient_2local, z_average_observable)
+from workloads.generators import Hamiltonian
 
 pytestmark = pytest.mark.gpu
 
@@ -286,6 +287,27 @@ def test_gradient_vs_oracle(sd, order, n):
     assert np.allclose(_host(t), psi0)   # state0 untouched
 
 
+def test_gradient_large_group(sd):
+    """A commuting group of 120 diagonal terms beside 12 X terms: the adjoint
+    kernel sums a group of more than 80 terms per warp instead of per thread;
+    value and gradient against the oracle (complex128, both orders)."""
+    rng = np.random.default_rng(59)
+    n = 12
+    z = rng.integers(1, 1 << n, size=120, dtype=np.uint64)
+    x = np.array([1 << (i % n) for i in range(12)], dtype=np.uint64)
+    h = Hamiltonian(n, np.concatenate([np.zeros(120, dtype=np.uint64), x]),
+                    np.concatenate([z, np.zeros(12, dtype=np.uint64)]), rng.uniform(-1, 1, 132))
+    psi0 = plus_state(n)
+    obs = z_average_observable(n)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    assert max(np.diff(sim.plan_view()["group_offsets"])) > 80
+    for order in (1, 2):
+        f, g = sim.grad(_dev(psi0, "c128"), 0.05, 3, obs, order)
+        f_ref, g_ref = oracle.grad(h, psi0, 0.05, 3, order, obs)
+        assert abs(f - f_ref) < 1e-12
+        assert np.max(np.abs(g - g_ref)) < 1e-9 * max(1.0, np.max(np.abs(g_ref)))
+
+
 @pytest.mark.parametrize("jit", [-1, 1])
 def test_gradient_complex64(sd, jit):
     """Complex64 states with FP64 reductions in the adjoint: value and
@@ -515,10 +537,11 @@ def test_paired_layout(sd, order):
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 def test_two_prefetch_buffers(sd, dtype):
-    """Run-time passes with two prefetch buffers (no barrier between a tile's
-    load and the next tile's prefetch) against the oracle: Heisenberg blocks,
-    CNOT permutations and S/CZ layers, several tiles per block, both orders,
-    and the paired layout."""
+    """Run-time passes with two prefetch buffers (two tiles in flight while a
+    block works on a third) against the oracle: Heisenberg blocks, CNOT
+    permutations and S/CZ layers, both orders, the paired layout, and a 2^22
+    state at the default tile size, where every block runs several tiles
+    through both buffers."""
     h = heisenberg_lattice(4, 4)
     _check(sd, h, basis_state(16, neel_index(4, 4)), 0.02, 6, 1, dtype, jit=1, prefetch=2)
     rng = np.random.default_rng(69)
@@ -527,6 +550,8 @@ def test_two_prefetch_buffers(sd, dtype):
     _check(sd, h2, _rand_state(rng, 15), 0.05, 2, 1, dtype, tile_bits=10, jit=1, prefetch=2)
     if dtype == "c64":
         _check(sd, h, basis_state(16, neel_index(4, 4)), 0.02, 6, 2, dtype, jit=1, layout=1, prefetch=2)
+    h3 = heisenberg_lattice(2, 11)
+    _check(sd, h3, _rand_state(rng, 22), 0.02, 5, 1, dtype, jit=1, prefetch=2)
 
 
 def test_autotune_shape(sd, tmp_path):
