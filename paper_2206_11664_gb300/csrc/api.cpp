@@ -252,9 +252,12 @@ sd_status schedule_for(sd_ctx *ctx, const Circuit &circ, bool dbl, Schedule &S, 
 
 // Whether a program of `passes` tile passes is compiled at run time: always
 // with jit = 1 (or SD_JIT=1), never with jit = -1 (or SD_JIT=0), else for
-// states of 20+ qubits and at most kJitMaxPasses passes.  One-shot programs
-// (the half steps that open and close a second-order evolution,
-// allow_jit = false) are not worth a compilation unless it is forced.
+// states of 20+ qubits and at most kJitMaxPasses passes.  The one-shot
+// program that opens a second-order evolution (group 1's half step,
+// allow_jit = false) is not worth a compilation unless it is forced.  The
+// closing program is the core with group 1's last exponential halved: the
+// same passes with other angles, whose generated source (angles are kernel
+// arguments) is the core's, so that its kernels come from the core's cache.
 bool jit_wanted(const sd_ctx *ctx, bool allow_jit, int64_t passes) {
     int mode = ctx->jit_opt;
     if (const char *e = getenv("SD_JIT")) mode = atoi(e) > 0 ? 1 : (e[0] == '0' ? -1 : mode);
@@ -420,7 +423,7 @@ sd_status get_program(sd_ctx *ctx, bool dbl, int order, int kind, double dt, Pro
     }
     auto P = std::make_unique<Program>();
     Circuit c = segment_circuit(ctx, order, kind, dt, reps);
-    sd_status s = build_program(ctx, c, dbl, *P, kind == 0 || kind == 2 || kind == 4);
+    sd_status s = build_program(ctx, c, dbl, *P, kind != 1);
     if (s != SD_OK) {
         free_program(*P);
         return s;
@@ -571,7 +574,7 @@ sd_status segment_passes(sd_ctx *ctx, bool dbl, int order, int kind, int reps, i
     Circuit c = segment_circuit(ctx, order, kind, 0.01, reps);
     canonicalize_1q(c, ctx->n);
     Schedule S;
-    sd_status s = schedule_for(ctx, c, dbl, S, pin0_wanted(ctx, dbl, kind == 0 || kind == 2 || kind == 4));
+    sd_status s = schedule_for(ctx, c, dbl, S, pin0_wanted(ctx, dbl, kind != 1));
     if (s == SD_OK) out = (int64_t)S.passes.size();
     return s;
 }
@@ -1167,7 +1170,7 @@ sd_status sd_precompile(sd_ctx *ctx, sd_dtype dtype, int64_t steps, int order, i
         Circuit c = segment_circuit(ctx, order, sg.first, 0.01, sg.second);
         canonicalize_1q(c, ctx->n);
         Schedule S;
-        const bool allow = sg.first == 0 || sg.first == 2 || sg.first == 4;
+        const bool allow = sg.first != 1;
         if ((s = schedule_for(ctx, c, dbl, S, pin0_wanted(ctx, dbl, allow))) != SD_OK) return s;
         S.prefetch = prefetch_buffers(ctx, dbl);
         if (!jit_wanted(ctx, allow, (int64_t)S.passes.size())) continue;
