@@ -1356,7 +1356,7 @@ sd_status sd_grad(sd_ctx *ctx, const void *d_state0, sd_dtype dtype, double dt, 
                 if ((s = run_program(ctx, dbl, *tr, phi, 1, st)) != SD_OK) return s;
                 if ((s = run_program(ctx, dbl, *tr, lam, 1, st)) != SD_OK) return s;
             }
-            CK(launch_grad_diag(dbl, phi, lam, ctx->n, gg->g, gg->masks_f, gg->qinv, tabs.tw,
+            CK(launch_grad_diag(dbl, phi, lam, ctx->n, gg->g, gg->masks_f, gg->qinv, tabs.fxt,
                                 ctx->d_partial, blocks, st));
             CK(launch_grad_finalize(ctx->d_partial, blocks, gg->g.m, gg->term_id, gg->factor,
                                     ctx->d_gacc, st));

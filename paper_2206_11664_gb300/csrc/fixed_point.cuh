@@ -70,12 +70,12 @@ constexpr long long kRsqrt2Q63 = 0x5A827999FCEF3242ll;
 // a * b / 2^62 for Q1.62 b (the 2 lowest bits dropped).
 SD_FX long long fx_mulq(long long a, long long b) { return __mul64hi(a, b) << 2; }
 
-// (re, im) <- (re, im) * e^{-2 pi i t} for Q0.64 turns t: t = k1 2^56 + k2 2^48 + r;
+// (Er, Ei) = e^{2 pi i t} in Q1.62 for Q0.64 turns t: t = k1 2^56 + k2 2^48 + r;
 // e^{2 pi i t} = T1[k1] T2[k2] e^{i phi}, phi = 2 pi r / 2^64 < 2 pi / 65536, with
 // cos phi = 1 - phi^2/2 and sin phi = phi - phi^3/6 (next terms below 2^-57).
 // T1 may carry a scale factor.
-SD_FX void fx_rotate(long long &re, long long &im, uint64_t t,
-                                          const longlong2 *__restrict__ T1, const longlong2 *__restrict__ T2) {
+SD_FX void fx_cis(uint64_t t, const longlong2 *__restrict__ T1, const longlong2 *__restrict__ T2,
+                  long long &Er, long long &Ei) {
     const longlong2 e1 = T1[t >> 56], e2 = T2[(t >> 48) & 255u];
     const unsigned long long r = t & 0xffffffffffffull;
     const unsigned long long p = __umul64hi(r << 16, kTwoPiQ61);  // phi 2^77
@@ -85,8 +85,15 @@ SD_FX void fx_rotate(long long &re, long long &im, uint64_t t,
     const long long sn = (long long)(p >> 15) - (long long)__umul64hi(p3 >> 41, 0x2AAAAAAAAAAAAAABull);
     const long long xr = fx_mulq(e1.x, e2.x) - fx_mulq(e1.y, e2.y);
     const long long xi = fx_mulq(e1.x, e2.y) + fx_mulq(e1.y, e2.x);
-    const long long Er = fx_mulq(xr, c) - fx_mulq(xi, sn);
-    const long long Ei = fx_mulq(xr, sn) + fx_mulq(xi, c);
+    Er = fx_mulq(xr, c) - fx_mulq(xi, sn);
+    Ei = fx_mulq(xr, sn) + fx_mulq(xi, c);
+}
+
+// (re, im) <- (re, im) * e^{-2 pi i t} for Q0.64 turns t (fx_cis).
+SD_FX void fx_rotate(long long &re, long long &im, uint64_t t,
+                     const longlong2 *__restrict__ T1, const longlong2 *__restrict__ T2) {
+    long long Er, Ei;
+    fx_cis(t, T1, T2, Er, Ei);
     const long long nr = fx_mulq(re, Er) + fx_mulq(im, Ei);
     const long long ni = fx_mulq(im, Er) - fx_mulq(re, Ei);
     re = nr;

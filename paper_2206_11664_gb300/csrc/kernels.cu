@@ -721,7 +721,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restrict__ mu, int n,
                  DevGrad g, const uint64_t *__restrict__ masks_f, const int64_t *__restrict__ qinv,
-                 const double2 *__restrict__ tw, double *__restrict__ partial, int per_thread) {
+                 const longlong2 *__restrict__ fxt, double *__restrict__ partial, int per_thread) {
     using A = typename VT<T>::A;
     // per_thread: acc[j * blockDim.x + tid] is thread tid's own sum for term
     // j (one add per term and chunk, reduced once at the end); otherwise
@@ -779,11 +779,18 @@ grad_diag_kernel(typename VT<T>::A *__restrict__ chi, typename VT<T>::A *__restr
 #pragma unroll
             for (int s = 0; s < 16; s++) {
                 // one rotation factor e^{-2 pi i G} for both vectors; in double
-                // precision by the table and series (the FP64 rate of this GPU
-                // makes sincospi the kernel's largest cost)
+                // precision its cosine and sine come from the Q1.62 tables and
+                // series in integer arithmetic, which leaves the FP64 pipe (the
+                // kernel's bound on this GPU) to the products with chi and mu
                 T sn, cs;
-                if constexpr (sizeof(T) == 8) turns_cs_tw(G[s], tw, cs, sn);
-                else turns_sc(G[s], sn, cs);
+                if constexpr (sizeof(T) == 8) {
+                    long long er, ei;
+                    fx_cis(G[s], fxt, fxt + 256, er, ei);
+                    cs = fx_to(er, -62);
+                    sn = fx_to(ei, -62);
+                } else {
+                    turns_sc(G[s], sn, cs);
+                }
                 A a = cv[s], b = mv[s];
                 chi[xf + s] = make_cplx<A>(a.x * cs + a.y * sn, a.y * cs - a.x * sn);
                 mu[xf + s] = make_cplx<A>(b.x * cs + b.y * sn, b.y * cs - b.x * sn);
@@ -981,7 +988,7 @@ int grad_blocks(int n, int num_sms) {
 }
 
 cudaError_t launch_grad_diag(bool dbl, void *chi, void *mu, int n, const DevGrad &g,
-                             const uint64_t *masks_f, const int64_t *qinv, const double2 *tw,
+                             const uint64_t *masks_f, const int64_t *qinv, const longlong2 *fxt,
                              double *partial, int blocks, cudaStream_t st) {
     // per-thread term sums while they fit beside nothing else in shared memory
     constexpr int kThreads = 256;
@@ -997,11 +1004,11 @@ cudaError_t launch_grad_diag(bool dbl, void *chi, void *mu, int n, const DevGrad
     if (dbl)
         grad_diag_kernel<double><<<blocks, kThreads, smem, st>>>(reinterpret_cast<double2 *>(chi),
                                                                  reinterpret_cast<double2 *>(mu), n, g,
-                                                                 masks_f, qinv, tw, partial, per_thread);
+                                                                 masks_f, qinv, fxt, partial, per_thread);
     else
         grad_diag_kernel<float><<<blocks, kThreads, smem, st>>>(reinterpret_cast<float2 *>(chi),
                                                                 reinterpret_cast<float2 *>(mu), n, g,
-                                                                masks_f, qinv, tw, partial, per_thread);
+                                                                masks_f, qinv, fxt, partial, per_thread);
     return cudaGetLastError();
 }
 

@@ -110,7 +110,7 @@ struct DevGrad {
 };
 cudaError_t launch_grad_diag(bool dbl, void *chi, void *mu, int n, const DevGrad &g,
                              const uint64_t *masks_f, const int64_t *qinv,
-                             const double2 *tw, double *partial, int blocks,
+                             const longlong2 *fxt, double *partial, int blocks,
                              cudaStream_t st);
 int grad_blocks(int n, int num_sms);
 

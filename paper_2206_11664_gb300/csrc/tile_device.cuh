@@ -185,24 +185,6 @@ __device__ __forceinline__ double2 rotate_tw(double2 a, uint64_t t, const double
 }
 
 
-
-// (cos 2 pi t, sin 2 pi t) for Q0.64 turns t in double precision: the top 8
-// bits of t index the table tw of e^{2 pi i k/256}; the remaining 52 bits
-// (exact as a double through the 2^52 mantissa trick) give the angle
-// phi < 2 pi/256, whose cosine and sine come from their Taylor series
-// (truncation below 1e-18), as in rotate_tw.
-__device__ __forceinline__ void turns_cs_tw(uint64_t t, const double2 *__restrict__ tw, double &c, double &s) {
-    const double2 e = tw[t >> 56];
-    const uint64_t r = (t << 8) >> 12;
-    const double ru = __longlong_as_double((long long)(0x4330000000000000ull | r)) - 4503599627370496.0;
-    const double phi = ru * (6.283185307179586 / 256.0 / 4503599627370496.0);
-    const double p2 = phi * phi;
-    const double cp = fma(p2, fma(p2, fma(p2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
-    const double sp = phi * fma(p2, fma(p2, fma(p2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
-    c = e.x * cp - e.y * sp;
-    s = e.y * cp + e.x * sp;
-}
-
 // e^{-2 pi i t} (times sc) applied to the two amplitudes of a packed pair
 // (R = their real parts, I = their imaginary parts), for Q0.32 turns t0 and
 // t1: the top 9 bits index tables of cos and sin of 2 pi k/512 (TC, TS); the
@@ -368,7 +350,6 @@ __device__ __forceinline__ void phase_apply(A *a, uint64_t xf, const int *gq, co
         a[s] = mul_ipow(a[s], k);
     }
 }
-
 
 
 // Signed sum over a warp's strided share of `count` tile-constant terms,

@@ -76,12 +76,24 @@ int main() {
         if (e > worst) worst = e;
     }
     if (worst > 1e-15) { std::printf("rotation error %g\n", worst); bad++; }
+    // cos and sin of 2 pi t in Q1.62, then as doubles (the adjoint kernel's rotation factor)
+    double worst_cs = 0;
+    for (int k = 0; k < 200000; k++) {
+        const uint64_t t = k < 4 ? (uint64_t)k << 62 : g();
+        const long double th = 2 * pi * (long double)t / 18446744073709551616.0L;
+        long long er, ei;
+        fx_cis(t, T1, T2, er, ei);
+        const double c = fx_to(er, -62), s = fx_to(ei, -62);
+        const double e = (double)(fabsl(c - cosl(th)) + fabsl(s - sinl(th)));
+        if (e > worst_cs) worst_cs = e;
+    }
+    if (worst_cs > 2e-16) { std::printf("cis error %g\n", worst_cs); bad++; }
     // quarter turns
     long long a = 5, b = 7;
     fx_mul_ipow(a, b, 1);
     if (a != -7 || b != 5) { std::printf("i^1\n"); bad++; }
     fx_mul_ipow(a, b, 3);
     if (a != 5 || b != 7) { std::printf("i^3\n"); bad++; }
-    std::printf("fixed point: %s (rotation error %.3g)\n", bad ? "FAILED" : "ok", worst);
+    std::printf("fixed point: %s (rotation error %.3g, cis error %.3g)\n", bad ? "FAILED" : "ok", worst, worst_cs);
     return bad ? 1 : 0;
 }

@@ -2,7 +2,8 @@
 compiled as host C++ and checked against long-double arithmetic: conversions
 between doubles and the tile's 64-bit units (round trip within one unit,
 headroom, correct rounding), the Q1.62 table-and-series rotation (error
-below 1e-15 relative), quarter turns."""
+below 1e-15 relative), its cosine and sine rounded to doubles (the adjoint
+kernel's rotation factor, within 2e-16), quarter turns."""
 import os
 import shutil
 import subprocess
