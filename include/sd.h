@@ -321,9 +321,9 @@ sd_status sd_prepare_batch(sd_ctx *const *ctxs, void *const *d_states, int64_t c
  * so for observables with many terms on large states it is slower than
  * sd_expect.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
- * calls share the array, so calls that overlap on the GPU (other streams or
- * host threads) race and must be serialised by the caller. */
+ * that device current.  All calls share the array, so calls that overlap on
+ * the GPU (other streams or host threads) race and must be serialised by the
+ * caller. */
 sd_status sd_expect_noalloc(int n, const void *d_state, sd_dtype dtype, int64_t mo,
                             const uint64_t *ox, const uint64_t *oz, const double *oc,
                             double *out_host, void *cuda_stream);
