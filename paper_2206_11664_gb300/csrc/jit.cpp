@@ -238,15 +238,10 @@ struct C64Rounds {
     void reset() {
         for (auto &r : rep) r = SlotRep{};
     }
-    bool all_plain() const {
-        for (auto &r : rep)
-            if (!rep_plain(r)) return false;
-        return true;
-    }
-    // instructions that bring every slot back to the plain representation
-    int fixup_cost() const {
+    // instructions that bring the slots rp back to the plain representation
+    static int fixup_cost(const SlotRep *rp) {
         int c = 0;
-        for (auto &r : rep) c += rep_plain(r) ? 0 : (r.sw ? 2 : 1);
+        for (int s = 0; s < 16; s++) c += rep_plain(rp[s]) ? 0 : (rp[s].sw ? 2 : 1);
         return c;
     }
     static bool packable(const SlotRep *rp, int I, int PA) {
@@ -330,9 +325,7 @@ struct C64Rounds {
             for (int s = 0; s < 16; s++)
                 if (!((s >> I) & 1)) rp[s | (1 << I)] = rep_mul_i(rp[s], B);
             after_monos(S, R, k, rp);
-            int fix = 0;
-            for (auto &r : rp) fix += rep_plain(r) ? 0 : (r.sw ? 2 : 1);
-            pack = 16 + fix <= 32;
+            pack = 16 + fixup_cost(rp) <= 32;
         }
         if (!pack) {
             if (last) {
