@@ -50,8 +50,9 @@ def parse():
                     help="Trotter steps of the gradient workload's timed evaluation (500 in its configuration)")
     ap.add_argument("--tile-bits", dest="tile_bits", type=int, default=0,
                     help="tile size for the batch workload (0 = default)")
-    ap.add_argument("--prefetch", type=int, default=0, choices=[0, 1, 2],
-                    help="prefetch buffers of the passes compiled at run time (0 = the library's choice)")
+    ap.add_argument("--prefetch", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="prefetch buffers of the passes compiled at run time (0 = the library's choice; "
+                         "3 = two in passes without a group exponential)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the tile size (K = 11..13) and, for complex64, the register layout by "
                          "timing them first (sd_autotune_shape)")

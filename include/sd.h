@@ -103,21 +103,23 @@ typedef struct {
     /* Prefetch buffers of the passes compiled at run time: 1 = one (the
      * next tile is loaded into it once every thread has read the current
      * one); 2 = two (the next two tiles are in flight while a block works on
-     * a third; 64 KB more shared memory, used only where it fits); 0 =
-     * default (what sd_autotune_shape chose, else 1 for complex64 and 2 for
+     * a third; 64 KB more shared memory, used only where it fits); 3 = two
+     * in the passes without a group exponential, one in the others; 0 =
+     * default (what sd_autotune_shape chose, else 3 for complex64 and 2 for
      * complex128 states). */
     int prefetch;
     int reserved[2];
 } sd_plan_opts;
 
 /* Result of sd_autotune_shape: the shape kept, and milliseconds per step
- * for tile sizes K = 9..13 (last index) in the plain layout with one and two
- * prefetch buffers (first index 0, 1) and in the paired layout with one and
+ * for tile sizes K = 9..13 (last index) in the plain layout with one prefetch
+ * buffer and with the dtype's two-buffer form (prefetch 3 for complex64, 2
+ * for complex128) (first index 0, 1) and in the paired layout with the same
  * two (2, 3); 0 where not run. */
 typedef struct {
     int best_k;
     int best_layout;          /* -1 plain, 1 paired; 0 on the on-chip path */
-    int best_prefetch;        /* 1 or 2 prefetch buffers; 0 on the on-chip path */
+    int best_prefetch;        /* sd_plan_opts.prefetch value kept; 0 on the on-chip path */
     double ms[4][5];
 } sd_tune_result;
 
@@ -211,8 +213,9 @@ sd_status sd_autotune(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t steps, int
                       int kmax, int *best_k, double *times_ms);
 
 /* Shape autotuner: as sd_autotune, over tile sizes K = kmin..kmax and, for
- * states whose passes are compiled at run time, over the prefetch depth (1
- * or 2 buffers, see sd_plan_opts.prefetch) and, for complex64, both
+ * states whose passes are compiled at run time, over the prefetch depth (one
+ * buffer or the dtype's two-buffer form, see sd_plan_opts.prefetch) and, for
+ * complex64, both
  * register layouts (plain and paired, see sd_plan_opts.layout); the fastest
  * shape is kept for this dtype until the next sd_plan (a tile size, layout
  * or prefetch depth given to sd_plan overrides the tuned one).  Synchronous;

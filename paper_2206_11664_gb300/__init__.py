@@ -132,7 +132,7 @@ class Simulator:
         """Host planning.  jit: 0 automatic, 1 always, -1 never; grouping:
         0 first fit, 1 largest first, 2 DSATUR, 3 by |c|; layout of the
         complex64 run-time passes: 0 default, -1 plain, 1 paired; prefetch
-        buffers of the run-time passes: 0 default, 1 or 2 (see sd.h)."""
+        depth of the run-time passes: 0 default, 1, 2 or 3 (see sd.h)."""
         o = N.PlanOpts(skip_rule, tile_bits, jit, grouping, layout, prefetch)
         self._check(self._lib.sd_plan(self._h, ctypes.byref(o)))
         return self
@@ -223,7 +223,8 @@ class Simulator:
         self._check(self._lib.sd_autotune_shape(self._h, dtype, float(dt), int(steps), int(order), kmin, kmax,
                                                 ctypes.byref(r)))
         ms = {}
-        for li, (lay, pf) in enumerate(((-1, 1), (-1, 2), (1, 1), (1, 2))):
+        two = 2 if dtype == C128 else 3        # the dtype's two-buffer form
+        for li, (lay, pf) in enumerate(((-1, 1), (-1, two), (1, 1), (1, two))):
             for k in range(kmin, kmax + 1):
                 if r.ms[li][k - 9] > 0:
                     ms[f"{k},{lay},{pf}"] = float(r.ms[li][k - 9])

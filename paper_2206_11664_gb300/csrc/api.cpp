@@ -265,13 +265,16 @@ bool jit_wanted(const sd_ctx *ctx, bool allow_jit, int64_t passes) {
     return mode > 0 || (mode == 0 && allow_jit && ctx->n >= 20 && passes <= kJitMaxPasses);
 }
 
-// Prefetch buffers of the run-time passes: sd_plan's choice, else the tuned
-// one, else one for complex64 (its passes gain nothing from a second) and two
-// for complex128 (whose slower passes do).
+// Prefetch depth of the run-time passes (sd_plan_opts.prefetch): sd_plan's
+// choice, else the tuned one, else the dtype's two-buffer form: for
+// complex64 two buffers in the passes without a group exponential only (the
+// light passes wait on their loads; the exponential passes gain nothing), for
+// complex128 two in every pass.
+int two_buffer_form(bool dbl) { return dbl ? 2 : 3; }
 int prefetch_buffers(const sd_ctx *ctx, bool dbl) {
     if (ctx->prefetch_opt > 0) return ctx->prefetch_opt;
     const int t = ctx->tuned_prefetch[dbl ? 1 : 0];
-    return t > 0 ? t : (dbl ? 2 : 1);
+    return t > 0 ? t : two_buffer_form(dbl);
 }
 
 // With the paired layout, complex64 programs that will probably be compiled
@@ -871,7 +874,7 @@ sd_status sd_plan(sd_ctx *ctx, const sd_plan_opts *opts) {
         layout = opts->layout;
         prefetch = opts->prefetch;
         if (layout < -1 || layout > 1) return fail(ctx, SD_EINVAL, "layout must be -1, 0 or 1");
-        if (prefetch < 0 || prefetch > 2) return fail(ctx, SD_EINVAL, "prefetch must be 0, 1 or 2");
+        if (prefetch < 0 || prefetch > 3) return fail(ctx, SD_EINVAL, "prefetch must be 0, 1, 2 or 3");
         if (rule > 2) return fail(ctx, SD_EINVAL, "skip_rule must be -1, 0, 1 or 2");
         if (tb != 0 && (tb < 9 || tb > 13)) return fail(ctx, SD_EINVAL, "tile_bits must be 0 or 9..13");
         if (grouping < 0 || grouping > 3) return fail(ctx, SD_EINVAL, "grouping must be 0, 1, 2 or 3");
@@ -1112,7 +1115,7 @@ sd_status sd_autotune_shape(sd_ctx *ctx, sd_dtype dtype, double dt, int64_t step
     if (ctx && dtype == SD_C64 && ctx->layout_opt != 0) layouts.assign(1, ctx->layout_opt);
     else if (dtype == SD_C64 && jit) layouts.push_back(1);
     if (ctx && ctx->prefetch_opt != 0) depths.assign(1, ctx->prefetch_opt);
-    else if (jit) depths.push_back(2);
+    else if (jit) depths.push_back(two_buffer_form(dtype == SD_C128));
     std::vector<std::pair<int, int>> shapes;
     for (int L : layouts)
         for (int PF : depths) shapes.push_back({L, PF});

@@ -586,7 +586,9 @@ int prefetch_round(const Schedule &S, const DevPass &P, int hoist) {
 // flight while the block works on a third.
 size_t jit_pass_smem(const Schedule &S, const DevPass &P, size_t amp, int K, bool *two) {
     const size_t base = pass_smem_bytes(P, amp, K);
-    const bool t = S.prefetch > 1 && base + (amp << K) <= kTileSmemLimit;
+    // prefetch 3: two buffers in the passes without a group exponential only
+    const bool want = S.prefetch == 2 || (S.prefetch == 3 && !P.scale_in_diag);
+    const bool t = want && base + (amp << K) <= kTileSmemLimit;
     if (two) *two = t;
     return t ? base + (amp << K) : base;
 }

@@ -566,7 +566,7 @@ def test_autotune_shape(sd, tmp_path):
     res = sim.autotune_shape(sd.C64, 0.02, steps=4, order=1, kmin=12, kmax=13, cache=cache)
     assert not res["cached"]
     ms = {tuple(int(v) for v in k.split(",")): t for k, t in res["ms_per_step"].items()}
-    assert {lay for _, lay, _ in ms} == {-1, 1} and {pf for _, _, pf in ms} == {1, 2}
+    assert {lay for _, lay, _ in ms} == {-1, 1} and {pf for _, _, pf in ms} == {1, 3}
     assert all(t > 0 for t in ms.values())
     best = (res["tile_bits"], res["layout"], res["prefetch"])
     assert best in ms and ms[best] == min(ms.values())

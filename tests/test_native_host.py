@@ -250,7 +250,7 @@ def test_argument_validation_of_the_other_entry_points(sd):
     for bad in (-2, 2):
         o = N.PlanOpts(-1, 0, 0, 0, bad)
         assert lib.sd_plan(sim._h, ctypes.byref(o)) == N.SD_EINVAL
-    for bad in (-1, 3):
+    for bad in (-1, 4):
         o = N.PlanOpts(-1, 0, 0, 0, 0, bad)
         assert lib.sd_plan(sim._h, ctypes.byref(o)) == N.SD_EINVAL
 
