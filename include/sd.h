@@ -105,7 +105,7 @@ typedef struct {
      * one); 2 = two (the next two tiles are in flight while a block works on
      * a third; 64 KB more shared memory, used only where it fits); 3 = two
      * in the passes without a group exponential, one in the others; 0 =
-     * default (what sd_autotune_shape chose, else 3 for complex64 and 2 for
+     * default (what sd_autotune_shape chose, else 1 for complex64 and 2 for
      * complex128 states). */
     int prefetch;
     int reserved[2];

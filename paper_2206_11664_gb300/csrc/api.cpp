@@ -265,16 +265,18 @@ bool jit_wanted(const sd_ctx *ctx, bool allow_jit, int64_t passes) {
     return mode > 0 || (mode == 0 && allow_jit && ctx->n >= 20 && passes <= kJitMaxPasses);
 }
 
-// Prefetch depth of the run-time passes (sd_plan_opts.prefetch): sd_plan's
-// choice, else the tuned one, else the dtype's two-buffer form: for
+// The two-buffer prefetch form the shape autotuner tries for a dtype: for
 // complex64 two buffers in the passes without a group exponential only (the
 // light passes wait on their loads; the exponential passes gain nothing), for
 // complex128 two in every pass.
 int two_buffer_form(bool dbl) { return dbl ? 2 : 3; }
+// Prefetch depth of the run-time passes (sd_plan_opts.prefetch): sd_plan's
+// choice, else the tuned one, else one buffer for complex64 and two for
+// complex128.
 int prefetch_buffers(const sd_ctx *ctx, bool dbl) {
     if (ctx->prefetch_opt > 0) return ctx->prefetch_opt;
     const int t = ctx->tuned_prefetch[dbl ? 1 : 0];
-    return t > 0 ? t : two_buffer_form(dbl);
+    return t > 0 ? t : (dbl ? 2 : 1);
 }
 
 // With the paired layout, complex64 programs that will probably be compiled
