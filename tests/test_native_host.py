@@ -209,6 +209,21 @@ def test_precompile_generated_kernels(sd, tmp_path, monkeypatch):
     assert sd.Simulator(small.n, small.x, small.z, small.c).plan().precompile(sd.C64, 5, 1) == 0
 
 
+def test_closing_program_shares_the_core_kernels(sd, tmp_path, monkeypatch):
+    """A second-order call closes with the core whose last group-1 exponential
+    is halved.  Angles are kernel arguments, so that program's generated
+    passes are the core's: compiling a 3-step call (opening half step, two
+    cores, closing program) compiles one core's worth of NVRTC chunks (12
+    passes each), not two."""
+    monkeypatch.setenv("SD_JIT_CACHE", str(tmp_path))
+    h = heisenberg_lattice(4, 5)
+    sim = sd.Simulator(h.n, h.x, h.z, h.c).plan()
+    core = sim.count_passes(sd.C64, 2, 3) - sim.count_passes(sd.C64, 2, 2)
+    assert core > 0
+    assert sim.precompile(sd.C64, 3, 2) == -(-core // 12)
+    assert sim.precompile(sd.C64, 3, 2) == 0
+
+
 def test_argument_validation_of_the_other_entry_points(sd):
     """Argument errors of the entry points added beside sd_evolve are
     reported before any device work (no GPU needed)."""
